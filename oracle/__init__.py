@@ -1,0 +1,300 @@
+"""Serial FP64 CPU oracle of the OTM explicit step (test infrastructure).
+
+Only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline leg may import
+this package. The product path (the CUDA library and its binding) never touches it, and it
+imports nothing from the product: it is a plain C file compiled with gcc and driven through
+ctypes.
+
+Functions and the passages they follow (paper: arXiv 2206.08772):
+  search / grid_info / grid_cells  -- Algorithm 3 (linked-cell search), Sec. 3.5
+  lme                              -- Eq. 14 (local max-ent shape functions, Newton for lambda)
+  kinematics                       -- Eq. 9, Eq. 11 (MP position and F increment)
+  return_map                       -- Sec. 4.1 J2 finite plasticity, Sec. 4.2 Johnson-Cook flow,
+                                      heating and fracture
+  Sim                              -- Algorithm 1, the whole explicit step (Eq. 4-13 + the above)
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "otm_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+OK = 0
+ERR_ARG, ERR_OOM, ERR_LME_NOCONV, ERR_JACOBIAN = -1, -3, -4, -5
+ERR_NONFINITE, ERR_RETURNMAP_NOCONV, ERR_CAPACITY = -6, -7, -8
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc: serial, -O2, no floating-point contraction."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+               "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Material(C.Structure):
+    _fields_ = [("model", C.c_int32), ("fracture", C.c_int32),
+                ("E", C.c_double), ("nu", C.c_double), ("rho0", C.c_double),
+                ("sigma_y0", C.c_double), ("H", C.c_double),
+                ("A", C.c_double), ("B", C.c_double), ("n", C.c_double), ("C", C.c_double),
+                ("m", C.c_double), ("eps_dot0", C.c_double),
+                ("T_room", C.c_double), ("T_melt", C.c_double), ("chi", C.c_double), ("cp", C.c_double),
+                ("d1", C.c_double), ("d2", C.c_double), ("d3", C.c_double), ("d4", C.c_double),
+                ("d5", C.c_double)]
+
+
+class Params(C.Structure):
+    _fields_ = [("h", C.c_double), ("beta", C.c_double), ("rs2", C.c_double),
+                ("cell_size", C.c_double), ("dt", C.c_double), ("T0", C.c_double),
+                ("newton_tol", C.c_double), ("eps_stab", C.c_double),
+                ("max_newton", C.c_int32), ("n_materials", C.c_int32),
+                ("wall", C.c_int32), ("tool", C.c_int32),
+                ("wall_p", C.c_double * 3), ("wall_n", C.c_double * 3),
+                ("tool_x0", C.c_double), ("tool_tip_y", C.c_double), ("tool_rake", C.c_double),
+                ("tool_clear", C.c_double), ("tool_v", C.c_double), ("friction", C.c_double),
+                ("allow_insert", C.c_int32), ("allow_erode", C.c_int32),
+                ("mat", Material * 4)]
+
+
+_P = C.c_void_p
+_D = C.POINTER(C.c_double)
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = C.CDLL(_LIB)
+            L.orc_lme.restype = C.c_int
+            L.orc_lme.argtypes = [C.c_int64, _P, C.c_double, C.c_double, C.c_int32, _P, _P, _P, _P]
+            L.orc_return_map.restype = C.c_int
+            L.orc_return_map.argtypes = [_P, C.c_double, _P, _P, C.c_double, C.c_double, C.c_double,
+                                         _P, _P, _P, _P, _P, _P]
+            L.orc_search.restype = C.c_int64
+            L.orc_search.argtypes = [C.c_int64, _P, C.c_int64, _P, C.c_double, C.c_double, _P, _P,
+                                     C.c_int64]
+            L.orc_grid_info.restype = C.c_int
+            L.orc_grid_info.argtypes = [C.c_int64, _P, C.c_double, _P, _P]
+            L.orc_grid_cells.restype = C.c_int
+            L.orc_grid_cells.argtypes = [C.c_int64, _P, C.c_double, C.c_int64, _P, _P]
+            L.orc_kinematics.restype = None
+            L.orc_kinematics.argtypes = [C.c_int64, _P, _P, _P, _P, _P, _P, _P]
+            L.orc_sim_create.restype = _P
+            L.orc_sim_create.argtypes = [_P, C.c_int64, C.c_int64, _P, _P, _P, _P, _P, _P, _P]
+            L.orc_sim_destroy.restype = None
+            L.orc_sim_destroy.argtypes = [_P]
+            L.orc_sim_step.restype = C.c_int
+            L.orc_sim_step.argtypes = [_P]
+            L.orc_sim_counts.restype = None
+            L.orc_sim_counts.argtypes = [_P] + [_P] * 6
+            L.orc_sim_get.restype = C.c_int
+            L.orc_sim_get.argtypes = [_P, C.c_int32, _P, C.c_int64]
+            L.orc_sim_set.restype = C.c_int
+            L.orc_sim_set.argtypes = [_P, C.c_int32, _P, C.c_int64]
+            L.orc_sim_refresh.restype = C.c_int
+            L.orc_sim_refresh.argtypes = [_P]
+            assert L.orc_sizeof_params() == C.sizeof(Params)
+            assert L.orc_sizeof_material() == C.sizeof(Material)
+            _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def material_struct(m) -> Material:
+    """ctypes material from a scenarios.Material."""
+    s = Material()
+    s.model = 0 if m.model == "j2" else 1
+    s.fracture = 1 if m.fracture else 0
+    for k in ("E", "nu", "rho0", "sigma_y0", "H", "A", "B", "n", "C", "m", "eps_dot0",
+              "T_room", "T_melt", "chi", "cp"):
+        setattr(s, k, float(getattr(m, k)))
+    s.d1, s.d2, s.d3, s.d4, s.d5 = (float(v) for v in m.d)
+    return s
+
+
+def params_struct(prob) -> Params:
+    """ctypes parameters from a scenarios.Problem (all derived values taken from the problem)."""
+    P = Params()
+    P.h, P.beta, P.rs2, P.cell_size = prob.h, prob.beta, prob.rs2, prob.cell_size
+    P.dt, P.T0, P.newton_tol, P.eps_stab = prob.dt, prob.T0, prob.newton_tol, prob.eps_stab
+    P.max_newton = prob.max_newton
+    P.n_materials = len(prob.materials)
+    c = prob.contact
+    P.wall, P.tool = int(c.wall), int(c.tool)
+    for i in range(3):
+        P.wall_p[i] = c.wall_point[i]
+        P.wall_n[i] = c.wall_normal[i]
+    P.tool_x0, P.tool_tip_y = c.tool_x0, c.tool_tip_y
+    P.tool_rake, P.tool_clear = math.radians(c.tool_rake_deg), math.radians(c.tool_clearance_deg)
+    P.tool_v, P.friction = c.tool_velocity, c.friction
+    P.allow_insert = 0
+    P.allow_erode = int(any(m.fracture for m in prob.materials))
+    for i, m in enumerate(prob.materials):
+        P.mat[i] = material_struct(m)
+    return P
+
+
+# ------------------------------------------------------------------ standalone pieces
+
+def lme(d: np.ndarray, beta: float, tol_r: float, max_it: int = 50, lam0=None):
+    """LME shape functions of one point from d_a = x_p - x_a (n x 3). Returns
+    (status, N, dN, lambda, iterations)."""
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    n = d.shape[0]
+    lam = np.zeros(3) if lam0 is None else np.array(lam0, dtype=np.float64)
+    N = np.zeros(n)
+    dN = np.zeros((n, 3))
+    it = C.c_int32(0)
+    st = lib().orc_lme(n, _ptr(d), beta, tol_r, max_it, _ptr(lam), _ptr(N), _ptr(dN), C.byref(it))
+    return st, N, dN, lam, it.value
+
+
+def return_map(mat, dt: float, dF: np.ndarray, be_n: np.ndarray, ebar_n: float, T_n: float, J: float):
+    """One-MP constitutive update. Returns (status, sigma6, be6, ebar, T, q, failed)."""
+    m = material_struct(mat) if not isinstance(mat, Material) else mat
+    dF = np.ascontiguousarray(dF, dtype=np.float64).reshape(9)
+    be_n = np.ascontiguousarray(be_n, dtype=np.float64).reshape(6)
+    sig = np.zeros(6)
+    be = np.zeros(6)
+    eb, T, q = C.c_double(0), C.c_double(0), C.c_double(0)
+    failed = C.c_int32(0)
+    st = lib().orc_return_map(C.byref(m), dt, _ptr(dF), _ptr(be_n), ebar_n, T_n, J, _ptr(sig), _ptr(be),
+                              C.byref(eb), C.byref(T), C.byref(q), C.byref(failed))
+    return st, sig, be, eb.value, T.value, q.value, bool(failed.value)
+
+
+def search(node_x: np.ndarray, mp_x: np.ndarray, rs2: float, cell_size: float, cap: int | None = None):
+    """Linked-cell supports: (offsets int64[nm+1], ids int32[P]), IDs ascending per point."""
+    node_x = np.ascontiguousarray(node_x, dtype=np.float64)
+    mp_x = np.ascontiguousarray(mp_x, dtype=np.float64)
+    nm = mp_x.shape[0]
+    if cap is None:
+        cap = max(1024, 600 * nm)
+    off = np.zeros(nm + 1, np.int64)
+    ids = np.zeros(cap, np.int32)
+    tot = lib().orc_search(node_x.shape[0], _ptr(node_x), nm, _ptr(mp_x), rs2, cell_size, _ptr(off),
+                           _ptr(ids), cap)
+    if tot < 0:
+        raise RuntimeError(f"oracle search failed: {tot}")
+    return off, ids[:tot].copy()
+
+
+def grid(node_x: np.ndarray, cell_size: float):
+    """Linked-cell grid: (origin[3], dims[3], cell_start[n_cells+1], sorted node IDs)."""
+    node_x = np.ascontiguousarray(node_x, dtype=np.float64)
+    origin = np.zeros(3)
+    dims = np.zeros(3, np.int64)
+    st = lib().orc_grid_info(node_x.shape[0], _ptr(node_x), cell_size, _ptr(origin), _ptr(dims))
+    if st != OK:
+        raise RuntimeError(f"oracle grid failed: {st}")
+    nc = int(np.prod(dims))
+    cs = np.zeros(nc + 1, np.int64)
+    srt = np.zeros(node_x.shape[0], np.int32)
+    st = lib().orc_grid_cells(node_x.shape[0], _ptr(node_x), cell_size, nc, _ptr(cs), _ptr(srt))
+    if st != OK:
+        raise RuntimeError(f"oracle grid failed: {st}")
+    return origin, dims, cs, srt
+
+
+def kinematics(ids, N, dN, node_x, node_du):
+    ids = np.ascontiguousarray(ids, np.int32)
+    N = np.ascontiguousarray(N, np.float64)
+    dN = np.ascontiguousarray(dN, np.float64)
+    node_x = np.ascontiguousarray(node_x, np.float64)
+    node_du = np.ascontiguousarray(node_du, np.float64)
+    xp = np.zeros(3)
+    dF = np.zeros(9)
+    lib().orc_kinematics(ids.size, _ptr(ids), _ptr(N), _ptr(dN), _ptr(node_x), _ptr(node_du), _ptr(xp),
+                         _ptr(dF))
+    return xp, dF.reshape(3, 3)
+
+
+# ------------------------------------------------------------------ the whole step
+
+FIELDS = dict(node_x=(0, 3, np.float64), node_du=(1, 3, np.float64), node_mass=(2, 1, np.float64),
+              node_force=(3, 3, np.float64), mp_x=(4, 3, np.float64), F=(5, 9, np.float64),
+              be=(6, 6, np.float64), sigma=(7, 6, np.float64), vol=(8, 1, np.float64),
+              ebar=(9, 1, np.float64), T=(10, 1, np.float64), lam=(11, 3, np.float64),
+              offsets=(12, 1, np.int64), ids=(13, 1, np.int32), N=(14, 1, np.float64),
+              dN=(15, 3, np.float64), node_gid=(16, 1, np.int64), mp_gid=(17, 1, np.int64),
+              newton_it=(18, 1, np.int32), rate=(19, 1, np.float64))
+
+
+class Sim:
+    """The oracle's whole explicit OTM simulation (Algorithm 1) on a scenarios.Problem."""
+
+    def __init__(self, prob, params: Params | None = None):
+        L = lib()
+        self.prob = prob
+        self.params = params if params is not None else params_struct(prob)
+        a = [np.ascontiguousarray(v) for v in (
+            prob.node_x.astype(np.float64), prob.node_du0.astype(np.float64),
+            prob.node_flags.astype(np.uint8), prob.mp_x.astype(np.float64),
+            prob.mp_vol.astype(np.float64), prob.mp_mass.astype(np.float64),
+            prob.mp_material.astype(np.int32))]
+        self._h = L.orc_sim_create(C.byref(self.params), prob.n_nodes, prob.n_mps, *[_ptr(v) for v in a])
+        if not self._h:
+            raise MemoryError("oracle sim create failed")
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib().orc_sim_destroy(self._h)
+            self._h = None
+
+    def counts(self):
+        v = [C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64(), C.c_int32(), C.c_int64()]
+        lib().orc_sim_counts(self._h, *[C.byref(x) for x in v])
+        return dict(n_nodes=v[0].value, n_mps=v[1].value, n_pairs=v[2].value, step=v[3].value,
+                    err=v[4].value, err_id=v[5].value)
+
+    def step(self, n: int = 1) -> int:
+        for _ in range(n):
+            st = lib().orc_sim_step(self._h)
+            if st != OK:
+                return st
+        return OK
+
+    def get(self, name: str) -> np.ndarray:
+        code, width, dt = FIELDS[name]
+        c = self.counts()
+        if name.startswith("node"):
+            rows = c["n_nodes"]
+        elif name == "offsets":
+            rows = c["n_mps"] + 1
+        elif name in ("ids", "N", "dN"):
+            rows = c["n_pairs"]
+        else:
+            rows = c["n_mps"]
+        out = np.zeros((rows, width) if width > 1 else (rows,), dtype=dt)
+        st = lib().orc_sim_get(self._h, code, _ptr(out), out.nbytes)
+        if st != OK:
+            raise RuntimeError(f"get {name}: {st}")
+        return out
+
+    def set(self, name: str, value: np.ndarray):
+        code, width, dt = FIELDS[name]
+        v = np.ascontiguousarray(value, dtype=dt)
+        st = lib().orc_sim_set(self._h, code, _ptr(v), v.nbytes)
+        if st != OK:
+            raise RuntimeError(f"set {name}: {st}")
+
+    def refresh(self) -> int:
+        return lib().orc_sim_refresh(self._h)

@@ -1,0 +1,119 @@
+"""Oracle pins for the whole explicit step (Algorithm 1; Eq. 4-13).
+
+Pins: the homogeneous-deformation patch test (an affine nodal increment field gives
+dF = 1 + G at every MP and moves the MPs affinely, Eq. 9 and Eq. 11 with the LME linear
+reproducibility); rigid translation (F = 1, sigma = 0, exact shift); conservation identities
+of the lumped assembly (sum_I m_I = sum_p m_p from the partition of unity; sum_I r_I = 0 from
+sum_a grad N_a = 0); the rigid wall (no node below the plane, tangential increment kept);
+elastic energy conservation of the central-difference scheme, with a drift that shrinks with
+the time step."""
+import math
+
+import numpy as np
+import pytest
+
+import scenarios
+
+
+def small_rod(**kw):
+    kw.setdefault("h", 0.8e-3)
+    kw.setdefault("R", 3.2e-3)
+    kw.setdefault("L", 4.0e-3)
+    return scenarios.taylor_rod(**kw)
+
+
+def test_patch_test_affine_increment(orc):
+    p = small_rod(wall=False)
+    G = np.array([[2e-3, 1e-3, -5e-4], [-7e-4, -1e-3, 3e-4], [4e-4, 6e-4, 1.5e-3]])
+    p.node_du0 = p.node_x @ G.T
+    sim = orc.Sim(p)
+    xp0 = sim.get("mp_x").copy()
+    assert sim.step(1) == 0
+    F = sim.get("F").reshape(-1, 3, 3)
+    assert np.abs(F - (np.eye(3) + G)).max() <= 1e-12
+    assert np.abs(sim.get("mp_x") - (xp0 + xp0 @ G.T)).max() <= 1e-12 * p.h
+    v = sim.get("vol")
+    assert np.abs(v / p.mp_vol - np.linalg.det(np.eye(3) + G)).max() <= 1e-12
+    sig = sim.get("sigma")
+    assert np.abs(sig - sig[0]).max() <= 1e-9 * np.abs(sig[0]).max()
+    # the uniform stress is the constitutive response to dF = 1 + G from the virgin state
+    st, s_ref, *_ = orc.return_map(p.materials[0], p.dt, np.eye(3) + G, np.array([1., 1, 1, 0, 0, 0]), 0.0,
+                                   p.T0, np.linalg.det(np.eye(3) + G))
+    assert np.abs(sig[0] - s_ref).max() <= 1e-9 * np.abs(s_ref).max()
+
+
+def test_rigid_translation(orc):
+    p = small_rod(wall=False)
+    c = np.array([1.3e-6, -2.1e-6, 0.7e-6])
+    p.node_du0 = np.tile(c, (p.n_nodes, 1))
+    sim = orc.Sim(p)
+    xp0 = sim.get("mp_x").copy()
+    assert sim.step(3) == 0
+    assert np.abs(sim.get("F").reshape(-1, 3, 3) - np.eye(3)).max() <= 1e-13
+    assert np.abs(sim.get("sigma")).max() <= 1e-13 * p.materials[0].E   # rounding level
+    assert np.abs(sim.get("mp_x") - (xp0 + 3 * c)).max() <= 1e-13 * p.h
+
+
+def test_conservation_of_mass_and_zero_net_force(orc):
+    p = small_rod(L=6.4e-3)
+    sim = orc.Sim(p)
+    assert sim.step(4) == 0
+    m = sim.get("node_mass")
+    r = sim.get("node_force")
+    assert abs(m.sum() - p.mp_mass.sum()) <= 1e-12 * p.mp_mass.sum()
+    assert np.abs(r.sum(axis=0)).max() <= 1e-11 * np.abs(r).sum()
+    assert np.abs(r).max() > 0
+
+
+def test_wall_contact_keeps_nodes_above_plane(orc):
+    p = small_rod(L=4.8e-3)
+    sim = orc.Sim(p)
+    assert sim.step(6) == 0
+    x = sim.get("node_x")
+    assert x[:, 2].min() >= 0.0
+    bottom = np.abs(x[:, 2]) == 0.0
+    assert bottom.sum() >= 40          # the impact face sits on the wall
+    assert sim.get("ebar").max() > 0   # the impact yields the rod
+
+
+def _strain_energy(sim, p):
+    F = sim.get("F").reshape(-1, 3, 3)
+    b = F @ np.transpose(F, (0, 2, 1))
+    w, _ = np.linalg.eigh(b)
+    e = 0.5 * np.log(w)
+    tr = e.sum(1)
+    dev = e - tr[:, None] / 3
+    mat = p.materials[0]
+    W = 0.5 * mat.K * tr ** 2 + mat.mu * (dev * dev).sum(1)
+    return (p.mp_vol * W).sum()
+
+
+def _energy_at_step(sim, p):
+    """Total energy at time n: central velocity (du_n + du_n+1) / (2 dt), lumped mass m_I,n and
+    the Hencky strain energy of F_n; advances the simulation by one step."""
+    du_n = sim.get("node_du").copy()
+    se = _strain_energy(sim, p)
+    assert sim.step(1) == 0
+    m = sim.get("node_mass")
+    v = (du_n + sim.get("node_du")) / (2 * p.dt)
+    return se + 0.5 * (m * (v * v).sum(1)).sum()
+
+
+@pytest.mark.slow
+def test_elastic_energy_drift_shrinks_with_dt(orc):
+    drifts = []
+    for cfl, steps in ((0.3, 60), (0.15, 120)):
+        mat = scenarios.copper_j2()
+        mat.sigma_y0 = 1e30
+        p = small_rod(L=6.4e-3, wall=False, material=mat, cfl=cfl)
+        rate = 4e3                                           # axial velocity gradient [1/s]
+        zc = p.node_x[:, 2].mean()
+        p.node_du0 = np.zeros_like(p.node_x)
+        p.node_du0[:, 2] = rate * (p.node_x[:, 2] - zc) * p.dt
+        sim = orc.Sim(p)
+        e0 = _energy_at_step(sim, p)
+        assert sim.step(steps - 2) == 0
+        e1 = _energy_at_step(sim, p)
+        drifts.append(abs(e1 - e0) / e0)
+    assert drifts[0] < 5e-3                 # CFL 0.3, 60 steps
+    assert drifts[1] < 0.35 * drifts[0]      # second order in dt
