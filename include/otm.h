@@ -1,0 +1,190 @@
+/*
+ * otm.h -- C ABI of the GB300 explicit OTM material-point update.
+ *
+ * One explicit step of the Optimal Transportation Meshfree method (Kumar et al., "Parallel
+ * multiphysics simulation for the stabilized OTM method", arXiv 2206.08772, Algorithm 1):
+ *   1. lumped nodal mass and internal force           (Eq. 5, optional stabilisation Eq. 7-8)
+ *   2. central-difference nodal update + contact       (Eq. 4, Eq. 6; Sec. 4.1 wall, Sec. 4.2 tool)
+ *   3. material-point position, F, volume              (Eq. 9-13)
+ *   4. J2 / Johnson-Cook thermo-plastic return map     (Sec. 4.1, Sec. 4.2)
+ *   5. linked-cell support search                      (Algorithm 3)
+ *   6. local max-ent shape functions and gradients     (Eq. 14, Newton for lambda)
+ * all on one GPU in hand-written sm_103a kernels.
+ *
+ * Conventions
+ *  - Every call returns OTM_OK (0) or a negative OTM_ERR_* code; nothing aborts the process.
+ *  - Units are SI. Vectors are xyz triples. Symmetric tensors are 6-vectors in the order
+ *    (xx, yy, zz, xy, yz, xz). Full tensors are row-major 3x3 (F[3*i+j] = F_ij).
+ *  - Device memory: the library never allocates device memory. The caller passes one device
+ *    workspace (size from otm_workspace_bytes) that must stay valid until otm_destroy; all
+ *    state lives in it. The handle itself is a small host object.
+ *  - Host memory: otm_init reads the caller's host arrays (copied to the workspace before it
+ *    returns); otm_state copies into caller-owned host memory.
+ *  - Streams: all work is enqueued on the stream given to otm_init (a cudaStream_t passed as
+ *    void*; NULL = legacy default stream). Only otm_init, otm_step, otm_state and
+ *    otm_error_detail synchronise that stream.
+ *  - Fields come back in ascending ID order (erosion removes entries, never reorders them).
+ *  - After an error the state is that of the failing step, partially updated (the oracle
+ *    behaves the same way); otm_error_detail names the code and the smallest offending ID.
+ */
+#ifndef OTM_H
+#define OTM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OTM_OK 0
+#define OTM_ERR_ARG (-1)              /* bad argument, size or pointer */
+#define OTM_ERR_CUDA (-2)             /* a CUDA runtime call failed */
+#define OTM_ERR_WORKSPACE (-3)        /* workspace smaller than otm_workspace_bytes */
+#define OTM_ERR_LME_NOCONV (-4)       /* Newton for lambda did not converge (point outside hull) */
+#define OTM_ERR_JACOBIAN (-5)         /* det(dF) <= 0 or non-positive elastic stretch */
+#define OTM_ERR_NONFINITE (-6)        /* NaN / Inf in positions or stresses */
+#define OTM_ERR_RETURNMAP_NOCONV (-7) /* Johnson-Cook consistency iteration failed */
+#define OTM_ERR_CAPACITY (-8)         /* support / influence / cell capacity exceeded */
+
+#define OTM_PRECISION_FP64 0          /* every step in FP64 */
+#define OTM_PRECISION_MIXED 1         /* FP32 force scatter and node update, FP64 elsewhere */
+
+#define OTM_FLAG_FIXED 1              /* node flag: displacement increment held at zero */
+
+typedef struct otm_material {
+    int32_t model;      /* 0: J2 with linear isotropic hardening (Sec. 4.1); 1: Johnson-Cook (Sec. 4.2) */
+    int32_t fracture;   /* 1: Johnson-Cook fracture strain checked (erosion when allow_erode) */
+    double E, nu, rho0;
+    double sigma_y0, H;                 /* J2: initial yield stress, hardening modulus */
+    double A, B, n, C, m, eps_dot0;     /* JC flow stress */
+    double T_room, T_melt, chi, cp;     /* JC thermal softening, Taylor-Quinney, heat capacity */
+    double d1, d2, d3, d4, d5;          /* JC fracture */
+} otm_material;
+
+typedef struct otm_params {
+    double h;            /* characteristic nodal spacing (beta = gamma / h^2, Sec. 2.3) */
+    double beta;         /* LME locality parameter */
+    double rs2;          /* squared support radius: node in support iff |x_p - x_a|^2 <= rs2 */
+    double cell_size;    /* linked-cell edge, >= sqrt(rs2)/2 (stencil +-2 cells) */
+    double dt;           /* time step */
+    double T0;           /* initial temperature */
+    double newton_tol;   /* Newton stops when |sum N_a (x_p - x_a)| <= newton_tol * h */
+    double eps_stab;     /* stabilisation penalty of Eq. 7 (0 = off) */
+    int32_t max_newton;  /* Newton iteration limit */
+    int32_t n_materials; /* 1..4 */
+    int32_t precision;   /* OTM_PRECISION_FP64 or OTM_PRECISION_MIXED */
+    int32_t wall;        /* 1: rigid frictionless plane (wall_p, wall_n) */
+    int32_t tool;        /* 1: rigid moving cutting tool */
+    int32_t allow_erode; /* 1: MPs meeting the fracture criterion are removed */
+    double wall_p[3], wall_n[3];
+    double tool_x0, tool_tip_y, tool_rake, tool_clear, tool_v, friction; /* angles in radians */
+    int32_t max_support; /* per-MP support capacity (pair slots per MP), multiple of 32, <= 1024 */
+    int32_t reserved;
+    otm_material mat[4];
+} otm_params;
+
+typedef struct otm_problem {
+    int64_t n_nodes, n_mps;
+    const double *node_x;        /* n_nodes x 3, initial positions */
+    const double *node_du0;      /* n_nodes x 3, initial displacement increment (v0 * dt) */
+    const uint8_t *node_flags;   /* n_nodes, OTM_FLAG_* bits */
+    const double *mp_x;          /* n_mps x 3, initial positions */
+    const double *mp_vol;        /* n_mps, initial volumes */
+    const double *mp_mass;       /* n_mps, masses (constant) */
+    const int32_t *mp_material;  /* n_mps, index into params.mat */
+} otm_problem;
+
+typedef struct otm_handle otm_handle;
+
+/* Fields for otm_state (host copies, ID order). Sizes in bytes:
+ *  NODE_X, NODE_DU, NODE_FORCE: 24 n_nodes   NODE_MASS: 8 n_nodes   NODE_FLAGS: n_nodes
+ *  MP_X: 24 n_mps  F, DF: 72 n_mps  BE, SIGMA: 48 n_mps  VOL, EBAR, T, RATE: 8 n_mps
+ *  LAMBDA: 24 n_mps  SUPPORT_COUNT, NEWTON_IT: 4 n_mps
+ *  SUPPORT_IDS: 4 n_mps max_support (padded rows, row p holds SUPPORT_COUNT[p] IDs, ascending)
+ *  SHAPE: 32 n_mps max_support (padded rows of (N, dN/dx, dN/dy, dN/dz))
+ *  MP_GID, NODE_GID: 8 * count (original IDs of the surviving entries) */
+enum {
+    OTM_FIELD_NODE_X = 0, OTM_FIELD_NODE_DU = 1, OTM_FIELD_NODE_MASS = 2, OTM_FIELD_NODE_FORCE = 3,
+    OTM_FIELD_MP_X = 4, OTM_FIELD_F = 5, OTM_FIELD_BE = 6, OTM_FIELD_SIGMA = 7, OTM_FIELD_VOL = 8,
+    OTM_FIELD_EBAR = 9, OTM_FIELD_T = 10, OTM_FIELD_LAMBDA = 11, OTM_FIELD_SUPPORT_COUNT = 12,
+    OTM_FIELD_SUPPORT_IDS = 13, OTM_FIELD_SHAPE = 14, OTM_FIELD_NEWTON_IT = 15, OTM_FIELD_RATE = 16,
+    OTM_FIELD_DF = 17, OTM_FIELD_MP_GID = 18, OTM_FIELD_NODE_GID = 19, OTM_FIELD_NODE_FLAGS = 20
+};
+
+/* Bytes of device workspace needed for a problem of this size. */
+int otm_workspace_bytes(int64_t n_nodes, int64_t n_mps, const otm_params *params, size_t *bytes);
+
+/* Create a simulation: copy the host problem into the workspace, then build the initial
+ * supports and shape functions (Algorithm 1, REQUIRE line: initial node and MP sets).
+ * params is copied. workspace: device pointer, 256-byte aligned, ws_bytes >= required.
+ * On success *out is a new handle (free with otm_destroy). */
+int otm_init(const otm_problem *prob, const otm_params *params, void *stream, void *workspace,
+             size_t ws_bytes, otm_handle **out);
+
+/* Advance n_steps explicit steps (Algorithm 1, steps 1-6 each). Synchronises the stream at
+ * the end and returns the first error raised by any kernel (later steps are skipped). */
+int otm_step(otm_handle *h, int32_t n_steps);
+
+/* Same as otm_step but does not synchronise; errors are reported by otm_error_detail. */
+int otm_step_async(otm_handle *h, int32_t n_steps);
+
+/* Current sizes (host-side view; exact after otm_step returns). */
+int otm_counts(otm_handle *h, int64_t *n_nodes, int64_t *n_mps, int64_t *n_pairs, int64_t *step);
+
+/* Copy one field to host memory (bytes must equal the field size). Synchronises the stream. */
+int otm_state(otm_handle *h, int32_t field, void *host_dst, size_t bytes);
+
+/* Overwrite one field from host memory (NODE_X, NODE_DU, MP_X, F, BE, SIGMA, VOL, EBAR, T,
+ * LAMBDA). Supports and shape functions are rebuilt by otm_refresh. */
+int otm_set_state(otm_handle *h, int32_t field, const void *host_src, size_t bytes);
+
+/* Rebuild supports, shape functions and node-major lists from the current positions. */
+int otm_refresh(otm_handle *h);
+
+/* First error recorded on the device: its code and the smallest offending ID. Synchronises. */
+int otm_error_detail(otm_handle *h, int32_t *code, int64_t *first_id);
+
+/* Launch statistics: kernels enqueued since otm_init. */
+int otm_kernel_launches(otm_handle *h, int64_t *launches);
+
+void otm_destroy(otm_handle *h);
+
+/* ---------------------------------------------------------------------------------------
+ * Stand-alone kernels (device pointers, caller-owned; enqueued on `stream`, not synchronised)
+ * ------------------------------------------------------------------------------------- */
+
+/* Bytes of scratch needed by otm_support_search for n_nodes nodes. */
+int otm_search_scratch_bytes(int64_t n_nodes, size_t *bytes);
+
+/* Linked-cell support search (Algorithm 3; support definition as in otm_params.rs2).
+ * node_x: n_nodes x 3, mp_x: n_mps x 3 (device, FP64). Output: ids[p * max_support + k],
+ * k < counts[p], ascending node IDs; counts[p] is the full support size (> max_support means
+ * the row was truncated and status holds OTM_ERR_CAPACITY). Grid: origin = componentwise
+ * node minimum, dims = floor((max - min)/cell_size) + 1 per axis. scratch: device memory of
+ * otm_search_scratch_bytes; grid_out (optional, device): origin[3] doubles then dims[3] as
+ * doubles. status (device int32, caller zeroes it): 0 or the first error code. */
+int otm_support_search(const double *node_x, int64_t n_nodes, const double *mp_x, int64_t n_mps,
+                       double rs2, double cell_size, int32_t max_support, int32_t *ids,
+                       int32_t *counts, void *scratch, size_t scratch_bytes, double *grid_out,
+                       int32_t *status, void *stream);
+
+/* LME shape functions (Eq. 14) for n_mps points with given supports (ids/counts as produced
+ * by otm_support_search). lambda (n_mps x 3, in: start, out: solution). shape: n_mps x
+ * max_support x 4 doubles (N, dN/dx, dN/dy, dN/dz). iters (n_mps, optional). status: as above
+ * (OTM_ERR_LME_NOCONV on failure). */
+int otm_lme(const double *node_x, const double *mp_x, int64_t n_mps, const int32_t *ids,
+            const int32_t *counts, int32_t max_support, double beta, double tol_abs,
+            int32_t max_newton, double *lambda, double *shape, int32_t *iters, int32_t *status,
+            void *stream);
+
+/* Constitutive update (Sec. 4.1 / 4.2) of n_mps points: inputs dF (9), F_new (9, for J),
+ * be (6, in/out), ebar, T (in/out); outputs sigma (6), rate, failed (uint8, optional). */
+int otm_return_map(const otm_material *mat, double dt, int64_t n_mps, const double *dF,
+                   const double *F_new, double *be, double *ebar, double *T, double *sigma,
+                   double *rate, uint8_t *failed, int32_t *status, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OTM_H */

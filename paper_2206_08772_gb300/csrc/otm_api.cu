@@ -1,0 +1,450 @@
+// otm_api.cu -- the C ABI (include/otm.h): workspace layout, initialisation, the step driver
+// (Algorithm 1 as a fixed kernel sequence on one stream) and state transfer.
+#include <stdlib.h>
+#include <string.h>
+
+#include "otm_dev.cuh"
+
+using namespace otm;
+
+struct otm_handle {
+    Dev D;
+    otm_params P;
+    cudaStream_t stream;
+    void *ws;
+    size_t ws_bytes;
+    int32_t *scan_tmp;
+    int64_t step;
+    long long launches;
+};
+
+#define CK(call)                                  \
+    do {                                          \
+        cudaError_t e_ = (call);                  \
+        if (e_ != cudaSuccess) return OTM_ERR_CUDA; \
+    } while (0)
+
+static size_t a256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// Carve every array out of the workspace. With base == NULL only the size is computed.
+static size_t layout(int64_t nn, int64_t nm, int S, int precision, char *base, Dev *D, int32_t **scan_tmp)
+{
+    size_t off = 0;
+    const int64_t slots = nm * (int64_t)S;
+    const int max_cells = (int)(16 * nn + 65536);
+#define TAKE(ptr, T, count)                                         \
+    do {                                                            \
+        if (base) (ptr) = (T *)(base + off);                        \
+        off += a256((size_t)(count) * sizeof(T));                   \
+    } while (0)
+    Dev d;
+    memset(&d, 0, sizeof(d));
+    int32_t *tmp = nullptr;
+    TAKE(d.err, unsigned long long, 1);
+    TAKE(d.emax, int, 2);
+    TAKE(d.grid, GridDev, 1);
+    // nodes
+    TAKE(d.x, double4_32a, nn);
+    TAKE(d.x_prev, double4_32a, nn);
+    TAKE(d.du, double4_32a, nn);
+    TAKE(d.mr, double4_32a, nn);
+    TAKE(d.spos, double4_32a, nn);
+    TAKE(d.du32, float4, nn);
+    TAKE(d.nflags, uint8_t, nn);
+    TAKE(d.ngid, int64_t, nn);
+    TAKE(d.ncount, int32_t, nn);
+    TAKE(d.noff, int32_t, nn + 1);
+    TAKE(d.node_cell, int32_t, nn);
+    TAKE(d.node_rank, int32_t, nn);
+    TAKE(d.sorted, int32_t, nn);
+    TAKE(d.cell_count, int32_t, (int64_t)max_cells + 1);
+    TAKE(d.cell_start, int32_t, (int64_t)max_cells + 1);
+    TAKE(tmp, int32_t, scan_tmp_ints(nn + 1));
+    // material points
+    TAKE(d.xp, double4_32a, nm);
+    TAKE(d.F, double, 9 * nm);
+    TAKE(d.dF, double, 9 * nm);
+    TAKE(d.be, double, 6 * nm);
+    TAKE(d.sig, double, 6 * nm);
+    TAKE(d.vol, double, nm);
+    TAKE(d.mass, double, nm);
+    TAKE(d.ebar, double, nm);
+    TAKE(d.T, double, nm);
+    TAKE(d.rate, double, nm);
+    TAKE(d.Jdet, double, nm);
+    TAKE(d.lam, double, 3 * nm);
+    TAKE(d.mat_id, int32_t, nm);
+    TAKE(d.cnt, int32_t, nm);
+    TAKE(d.newton_it, int32_t, nm);
+    TAKE(d.failed, uint8_t, nm);
+    TAKE(d.mgid, int64_t, nm);
+    // pairs
+    TAKE(d.ids, int32_t, slots);
+    TAKE(d.shape, double4_32a, slots);
+    if (precision == OTM_PRECISION_MIXED) {
+        TAKE(d.contrib32, float4, slots);
+    } else {
+        TAKE(d.contrib64, double4_32a, slots);
+    }
+    TAKE(d.rank, uint16_t, slots);
+    TAKE(d.perm, uint32_t, slots);
+#undef TAKE
+    if (base) {
+        d.nn = nn;
+        d.nm = nm;
+        d.S = S;
+        d.precision = precision;
+        d.max_cells = max_cells;
+        *D = d;
+        *scan_tmp = tmp;
+    }
+    return off;
+}
+
+static int check_params(int64_t nn, int64_t nm, const otm_params *P)
+{
+    if (!P || nn <= 0 || nm <= 0) return OTM_ERR_ARG;
+    if (P->max_support < 32 || P->max_support > kMaxS || (P->max_support % 32) != 0) return OTM_ERR_ARG;
+    if (P->n_materials < 1 || P->n_materials > 4) return OTM_ERR_ARG;
+    if (P->precision != OTM_PRECISION_FP64 && P->precision != OTM_PRECISION_MIXED) return OTM_ERR_ARG;
+    if (!(P->h > 0) || !(P->beta > 0) || !(P->rs2 > 0) || !(P->dt > 0)) return OTM_ERR_ARG;
+    if (!(P->cell_size * 2.0 >= sqrt(P->rs2))) return OTM_ERR_ARG;   // stencil of +-2 cells
+    if (nm * (int64_t)P->max_support >= (int64_t)0x7fffffff) return OTM_ERR_ARG;
+    if (nn >= (int64_t)0x7fffffff / 16) return OTM_ERR_ARG;
+    if (P->eps_stab != 0.0) return OTM_ERR_ARG;   // stabilisation term: not in the CUDA path
+    return OTM_OK;
+}
+
+extern "C" int otm_workspace_bytes(int64_t n_nodes, int64_t n_mps, const otm_params *params, size_t *bytes)
+{
+    int st = check_params(n_nodes, n_mps, params);
+    if (st != OTM_OK) return st;
+    if (!bytes) return OTM_ERR_ARG;
+    *bytes = layout(n_nodes, n_mps, params->max_support, params->precision, nullptr, nullptr, nullptr) + 256;
+    return OTM_OK;
+}
+
+static void fill_params(Dev &D, const otm_params *P)
+{
+    D.h = P->h;
+    D.beta = P->beta;
+    D.rs2 = P->rs2;
+    D.cell = P->cell_size;
+    D.dt = P->dt;
+    D.tol_abs = P->newton_tol * P->h;
+    D.eps_stab = P->eps_stab;
+    D.max_newton = P->max_newton;
+    D.wall = P->wall;
+    D.tool = P->tool;
+    D.allow_erode = P->allow_erode;
+    for (int i = 0; i < 3; i++) {
+        D.wall_p[i] = P->wall_p[i];
+        D.wall_n[i] = P->wall_n[i];
+    }
+    D.tool_x0 = P->tool_x0;
+    D.tool_tip_y = P->tool_tip_y;
+    D.tool_rake = P->tool_rake;
+    D.tool_clear = P->tool_clear;
+    D.tool_v = P->tool_v;
+    D.friction = P->friction;
+    for (int i = 0; i < 4; i++) D.mat[i] = P->mat[i];
+}
+
+static int read_error(otm_handle *h, int32_t *code, int64_t *id)
+{
+    unsigned long long key = 0;
+    CK(cudaMemcpyAsync(&key, h->D.err, sizeof(key), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (key == ~0ULL) {
+        if (code) *code = OTM_OK;
+        if (id) *id = -1;
+        return OTM_OK;
+    }
+    const int c = -(int)(key & 0xff);
+    if (code) *code = c;
+    if (id) *id = (int64_t)(key >> 8);
+    return c;
+}
+
+// steps 5-6 of Algorithm 1 plus the node-major lists for the next step's step 1
+static int rebuild_supports(otm_handle *h)
+{
+    Dev &D = h->D;
+    cudaStream_t s = h->stream;
+    CK(launch_grid_build(D, s, &h->launches));
+    CK(cudaMemsetAsync(D.ncount, 0, (size_t)D.nn * sizeof(int32_t), s));
+    CK(cudaMemsetAsync(D.emax, 0x80, 2 * sizeof(int), s));
+    CK(launch_search_lme(D, false, s, &h->launches));
+    CK(launch_node_major_impl(D, h->scan_tmp, s, &h->launches));
+    return OTM_OK;
+}
+
+extern "C" int otm_init(const otm_problem *prob, const otm_params *params, void *stream, void *workspace,
+                        size_t ws_bytes, otm_handle **out)
+{
+    if (!prob || !params || !out || !workspace) return OTM_ERR_ARG;
+    *out = nullptr;
+    const int64_t nn = prob->n_nodes, nm = prob->n_mps;
+    int st = check_params(nn, nm, params);
+    if (st != OTM_OK) return st;
+    if (!prob->node_x || !prob->node_du0 || !prob->node_flags || !prob->mp_x || !prob->mp_vol || !prob->mp_mass ||
+        !prob->mp_material)
+        return OTM_ERR_ARG;
+    for (int64_t p = 0; p < nm; p++)
+        if (prob->mp_material[p] < 0 || prob->mp_material[p] >= params->n_materials) return OTM_ERR_ARG;
+    if (((uintptr_t)workspace) & 255) return OTM_ERR_ARG;
+    size_t need = layout(nn, nm, params->max_support, params->precision, nullptr, nullptr, nullptr);
+    if (ws_bytes < need) return OTM_ERR_WORKSPACE;
+
+    otm_handle *h = (otm_handle *)calloc(1, sizeof(otm_handle));
+    if (!h) return OTM_ERR_ARG;
+    h->P = *params;
+    h->stream = (cudaStream_t)stream;
+    h->ws = workspace;
+    h->ws_bytes = ws_bytes;
+    layout(nn, nm, params->max_support, params->precision, (char *)workspace, &h->D, &h->scan_tmp);
+    fill_params(h->D, params);
+    Dev &D = h->D;
+    cudaStream_t s = h->stream;
+    int rc = OTM_OK;
+    do {
+        // host problem -> workspace (positions staged through the pair-shape region)
+        double *stage = (double *)D.shape;
+        if ((size_t)nm * D.S * sizeof(double4_32a) < (size_t)3 * (nn > nm ? nn : nm) * sizeof(double)) {
+            rc = OTM_ERR_ARG;
+            break;
+        }
+        if (cudaMemsetAsync(D.err, 0xff, sizeof(unsigned long long), s) != cudaSuccess) { rc = OTM_ERR_CUDA; break; }
+        if (cudaMemcpyAsync(stage, prob->node_x, 24 * nn, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            launch_pack3to4(stage, nn, D.x, s, &h->launches) != cudaSuccess ||
+            cudaMemcpyAsync(stage, prob->node_du0, 24 * nn, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            launch_pack3to4(stage, nn, D.du, s, &h->launches) != cudaSuccess ||
+            cudaMemcpyAsync(stage, prob->mp_x, 24 * nm, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            launch_pack3to4(stage, nm, D.xp, s, &h->launches) != cudaSuccess ||
+            cudaMemcpyAsync(D.nflags, prob->node_flags, nn, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(D.vol, prob->mp_vol, 8 * nm, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(D.mass, prob->mp_mass, 8 * nm, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(D.mat_id, prob->mp_material, 4 * nm, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            launch_init_state(D, params->T0, s, &h->launches) != cudaSuccess) {
+            rc = OTM_ERR_CUDA;
+            break;
+        }
+        // the staging copies must land before the region is reused by the support build
+        if (cudaStreamSynchronize(s) != cudaSuccess) { rc = OTM_ERR_CUDA; break; }
+        rc = rebuild_supports(h);
+        if (rc != OTM_OK) break;
+        rc = read_error(h, nullptr, nullptr);
+    } while (0);
+    if (rc != OTM_OK) {
+        free(h);
+        return rc;
+    }
+    *out = h;
+    return OTM_OK;
+}
+
+static int enqueue_step(otm_handle *h)
+{
+    Dev &D = h->D;
+    cudaStream_t s = h->stream;
+    const double t_next = (double)(h->step + 1) * D.dt;
+    // 1-2: lumped mass / force (segmented reduction), central difference, contact, x update
+    CK(launch_node_update(D, t_next, s, &h->launches));
+    // 3: MP position, F, volume
+    CK(launch_kinematics(D, s, &h->launches));
+    // 4: constitutive update
+    CK(launch_return_map(D, s, &h->launches));
+    // 5-6: linked-cell search, LME shape functions, contributions, node-major lists
+    int rc = rebuild_supports(h);
+    if (rc != OTM_OK) return rc;
+    h->step++;
+    return OTM_OK;
+}
+
+extern "C" int otm_step_async(otm_handle *h, int32_t n_steps)
+{
+    if (!h || n_steps < 0) return OTM_ERR_ARG;
+    for (int32_t k = 0; k < n_steps; k++) {
+        int rc = enqueue_step(h);
+        if (rc != OTM_OK) return rc;
+    }
+    return OTM_OK;
+}
+
+extern "C" int otm_step(otm_handle *h, int32_t n_steps)
+{
+    int rc = otm_step_async(h, n_steps);
+    if (rc != OTM_OK) return rc;
+    return read_error(h, nullptr, nullptr);
+}
+
+extern "C" int otm_error_detail(otm_handle *h, int32_t *code, int64_t *first_id)
+{
+    if (!h) return OTM_ERR_ARG;
+    int c = 0;
+    int64_t id = -1;
+    int rc = read_error(h, &c, &id);
+    if (rc == OTM_ERR_CUDA) return rc;
+    if (code) *code = c;
+    if (first_id) *first_id = id;
+    return OTM_OK;
+}
+
+extern "C" int otm_counts(otm_handle *h, int64_t *n_nodes, int64_t *n_mps, int64_t *n_pairs, int64_t *step)
+{
+    if (!h) return OTM_ERR_ARG;
+    if (n_nodes) *n_nodes = h->D.nn;
+    if (n_mps) *n_mps = h->D.nm;
+    if (step) *step = h->step;
+    if (n_pairs) {
+        int32_t tot = 0;
+        CK(cudaMemcpyAsync(&tot, h->D.noff + h->D.nn, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        *n_pairs = tot;
+    }
+    return OTM_OK;
+}
+
+extern "C" int otm_kernel_launches(otm_handle *h, int64_t *launches)
+{
+    if (!h || !launches) return OTM_ERR_ARG;
+    *launches = h->launches;
+    return OTM_OK;
+}
+
+struct FieldView {
+    const void *src;   // device base
+    size_t pitch;      // device row pitch
+    size_t width;      // bytes per row copied
+    size_t rows;
+};
+
+static bool field_view(otm_handle *h, int32_t f, FieldView *v)
+{
+    const Dev &D = h->D;
+    const size_t nn = (size_t)D.nn, nm = (size_t)D.nm, S = (size_t)D.S;
+    switch (f) {
+    case OTM_FIELD_NODE_X: *v = {D.x, 32, 24, nn}; return true;
+    case OTM_FIELD_NODE_DU: *v = {D.du, 32, 24, nn}; return true;
+    case OTM_FIELD_NODE_MASS: *v = {D.mr, 32, 8, nn}; return true;
+    case OTM_FIELD_NODE_FORCE: *v = {(const char *)D.mr + 8, 32, 24, nn}; return true;
+    case OTM_FIELD_NODE_FLAGS: *v = {D.nflags, 1, 1, nn}; return true;
+    case OTM_FIELD_MP_X: *v = {D.xp, 32, 24, nm}; return true;
+    case OTM_FIELD_F: *v = {D.F, 72, 72, nm}; return true;
+    case OTM_FIELD_DF: *v = {D.dF, 72, 72, nm}; return true;
+    case OTM_FIELD_BE: *v = {D.be, 48, 48, nm}; return true;
+    case OTM_FIELD_SIGMA: *v = {D.sig, 48, 48, nm}; return true;
+    case OTM_FIELD_VOL: *v = {D.vol, 8, 8, nm}; return true;
+    case OTM_FIELD_EBAR: *v = {D.ebar, 8, 8, nm}; return true;
+    case OTM_FIELD_T: *v = {D.T, 8, 8, nm}; return true;
+    case OTM_FIELD_RATE: *v = {D.rate, 8, 8, nm}; return true;
+    case OTM_FIELD_LAMBDA: *v = {D.lam, 24, 24, nm}; return true;
+    case OTM_FIELD_SUPPORT_COUNT: *v = {D.cnt, 4, 4, nm}; return true;
+    case OTM_FIELD_NEWTON_IT: *v = {D.newton_it, 4, 4, nm}; return true;
+    case OTM_FIELD_SUPPORT_IDS: *v = {D.ids, 4 * S, 4 * S, nm}; return true;
+    case OTM_FIELD_SHAPE: *v = {D.shape, 32 * S, 32 * S, nm}; return true;
+    case OTM_FIELD_MP_GID: *v = {D.mgid, 8, 8, nm}; return true;
+    case OTM_FIELD_NODE_GID: *v = {D.ngid, 8, 8, nn}; return true;
+    default: return false;
+    }
+}
+
+extern "C" int otm_state(otm_handle *h, int32_t field, void *host_dst, size_t bytes)
+{
+    if (!h || !host_dst) return OTM_ERR_ARG;
+    FieldView v;
+    if (!field_view(h, field, &v)) return OTM_ERR_ARG;
+    if (bytes != v.width * v.rows) return OTM_ERR_ARG;
+    if (v.rows == 0) return OTM_OK;
+    if (v.pitch == v.width)
+        CK(cudaMemcpyAsync(host_dst, v.src, bytes, cudaMemcpyDeviceToHost, h->stream));
+    else
+        CK(cudaMemcpy2DAsync(host_dst, v.width, v.src, v.pitch, v.width, v.rows, cudaMemcpyDeviceToHost,
+                             h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return OTM_OK;
+}
+
+extern "C" int otm_set_state(otm_handle *h, int32_t field, const void *host_src, size_t bytes)
+{
+    if (!h || !host_src) return OTM_ERR_ARG;
+    switch (field) {
+    case OTM_FIELD_NODE_X: case OTM_FIELD_NODE_DU: case OTM_FIELD_MP_X: case OTM_FIELD_F:
+    case OTM_FIELD_BE: case OTM_FIELD_SIGMA: case OTM_FIELD_VOL: case OTM_FIELD_EBAR: case OTM_FIELD_T:
+    case OTM_FIELD_LAMBDA: break;
+    default: return OTM_ERR_ARG;
+    }
+    FieldView v;
+    field_view(h, field, &v);
+    if (bytes != v.width * v.rows) return OTM_ERR_ARG;
+    if (v.pitch == v.width)
+        CK(cudaMemcpyAsync((void *)v.src, host_src, bytes, cudaMemcpyHostToDevice, h->stream));
+    else
+        CK(cudaMemcpy2DAsync((void *)v.src, v.pitch, host_src, v.width, v.width, v.rows, cudaMemcpyHostToDevice,
+                             h->stream));
+    if (field == OTM_FIELD_NODE_DU)   // keep the FP32 copy of the increments in step
+        CK(launch_du_to_f32(h->D, h->stream, &h->launches));
+    CK(cudaStreamSynchronize(h->stream));
+    return OTM_OK;
+}
+
+extern "C" int otm_refresh(otm_handle *h)
+{
+    if (!h) return OTM_ERR_ARG;
+    CK(cudaMemsetAsync(h->D.err, 0xff, sizeof(unsigned long long), h->stream));
+    int rc = rebuild_supports(h);
+    if (rc != OTM_OK) return rc;
+    return read_error(h, nullptr, nullptr);
+}
+
+extern "C" void otm_destroy(otm_handle *h)
+{
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    free(h);
+}
+
+// ------------------------------------------------------------------ stand-alone entries
+extern "C" int otm_search_scratch_bytes(int64_t n_nodes, size_t *bytes)
+{
+    if (n_nodes <= 0 || !bytes) return OTM_ERR_ARG;
+    *bytes = search_scratch_bytes(n_nodes);
+    return OTM_OK;
+}
+
+extern "C" int otm_support_search(const double *node_x, int64_t n_nodes, const double *mp_x, int64_t n_mps,
+                                  double rs2, double cell_size, int32_t max_support, int32_t *ids, int32_t *counts,
+                                  void *scratch, size_t scratch_bytes, double *grid_out, int32_t *status,
+                                  void *stream)
+{
+    if (!node_x || !mp_x || !ids || !counts || !scratch || !status || n_nodes <= 0 || n_mps < 0) return OTM_ERR_ARG;
+    if (max_support < 1 || max_support > kMaxS) return OTM_ERR_ARG;
+    if (!(rs2 > 0) || !(cell_size * 2.0 >= sqrt(rs2))) return OTM_ERR_ARG;
+    if (((uintptr_t)scratch) & 255) return OTM_ERR_ARG;
+    if (scratch_bytes < search_scratch_bytes(n_nodes)) return OTM_ERR_WORKSPACE;
+    CK(launch_search_only(node_x, n_nodes, mp_x, n_mps, rs2, cell_size, max_support, ids, counts, scratch,
+                          scratch_bytes, grid_out, status, (cudaStream_t)stream));
+    return OTM_OK;
+}
+
+extern "C" int otm_lme(const double *node_x, const double *mp_x, int64_t n_mps, const int32_t *ids,
+                       const int32_t *counts, int32_t max_support, double beta, double tol_abs, int32_t max_newton,
+                       double *lambda, double *shape, int32_t *iters, int32_t *status, void *stream)
+{
+    if (!node_x || !mp_x || !ids || !counts || !lambda || !shape || !status || n_mps < 0) return OTM_ERR_ARG;
+    if (max_support < 1 || max_support > kMaxS || !(beta > 0) || !(tol_abs > 0)) return OTM_ERR_ARG;
+    CK(launch_lme_only(node_x, mp_x, n_mps, ids, counts, max_support, beta, tol_abs, max_newton, lambda, shape,
+                       iters, status, (cudaStream_t)stream));
+    return OTM_OK;
+}
+
+extern "C" int otm_return_map(const otm_material *mat, double dt, int64_t n_mps, const double *dF,
+                              const double *F_new, double *be, double *ebar, double *T, double *sigma, double *rate,
+                              uint8_t *failed, int32_t *status, void *stream)
+{
+    if (!mat || !dF || !F_new || !be || !ebar || !T || !sigma || !status || n_mps < 0 || !(dt > 0))
+        return OTM_ERR_ARG;
+    CK(launch_return_map_only(mat, dt, n_mps, dF, F_new, be, ebar, T, sigma, rate, failed, status,
+                              (cudaStream_t)stream));
+    return OTM_OK;
+}

@@ -1,0 +1,214 @@
+// otm_dev.cuh -- device-side state and helpers shared by the OTM kernels (sm_103a).
+//
+// Layout in HBM (all carved from the caller's workspace, see otm_api.cu):
+//   nodes  : x, x_prev, du (double4_32a, w unused), du32 (float4, mixed path), mass/force (double4_32a),
+//            flags, influence counts, node-major offsets, linked-cell arrays
+//   MPs    : x_p (double4_32a), F, dF (9), b^e, sigma (6), vol, mass, ebar, T, rate, J, lambda (3),
+//            material, support count, Newton iterations, failure flag, original ID
+//   pairs  : padded MP-major rows of S slots: node ID (int32), shape (double4_32a: N, grad N),
+//            contribution (double4_32a or float4: m_p N, -v sigma grad N), rank in node list
+//            (uint16), and the node-major permutation of slot indices (uint32)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/otm.h"
+
+namespace otm {
+
+constexpr int kWarp = 32;
+constexpr int kMaxS = 1024;          // largest per-MP support capacity
+constexpr int kNodeSegMax = 4096;    // largest influence list reduced in shared memory
+constexpr int kSearchWarps = 4;      // warps per block in the search + LME kernel
+constexpr int kNodeWarps = 4;        // warps per block in the node kernel
+
+struct GridDev {
+    unsigned long long key_lo[3];    // ordered-integer keys of the node bounding box
+    unsigned long long key_hi[3];
+    double origin[3];
+    int dims[3];
+    int n_cells;                     // 0 when the grid is invalid (error raised)
+};
+
+struct Dev {
+    // sizes and parameters
+    int64_t nn, nm;
+    int S;                           // pair slots per MP
+    int precision;
+    int max_cells;
+    double h, beta, rs2, cell, dt, tol_abs, eps_stab;
+    int max_newton;
+    int wall, tool, allow_erode;
+    double wall_p[3], wall_n[3];
+    double tool_x0, tool_tip_y, tool_rake, tool_clear, tool_v, friction;
+    otm_material mat[4];
+
+    // nodes
+    double4_32a *x, *x_prev, *du, *mr;   // mr = (mass, force xyz) of the last node update
+    float4 *du32;
+    uint8_t *nflags;
+    int64_t *ngid;
+    int32_t *ncount, *noff;          // influence counts (atomics) and node-major offsets
+    // linked cell
+    GridDev *grid;
+    int32_t *cell_count, *cell_start, *node_cell, *node_rank, *sorted;
+    double4_32a *spos;                   // node positions in (cell, ID) order, w = ID bits
+    // material points
+    double4_32a *xp;
+    double *F, *dF, *be, *sig, *vol, *mass, *ebar, *T, *rate, *Jdet, *lam;
+    int32_t *mat_id, *cnt, *newton_it;
+    uint8_t *failed;
+    int64_t *mgid;
+    // pairs
+    int32_t *ids;
+    double4_32a *shape;
+    double4_32a *contrib64;
+    float4 *contrib32;
+    uint16_t *rank;
+    uint32_t *perm;
+    // status: (first offending id << 8) | (-code), atomicMin
+    unsigned long long *err;
+    int *emax;                       // largest binary exponent of the mass / force terms (2 ints)
+};
+
+// scratch of the stand-alone support search (carved from caller memory)
+struct SearchScratch {
+    GridDev *g;
+    double4_32a *x4, *spos;
+    int32_t *cell_count, *cell_start, *node_cell, *node_rank, *sorted;
+    unsigned long long *err;
+    int max_cells;
+};
+
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ void raise_error(unsigned long long *err, int code, long long id)
+{
+    unsigned long long key = ((unsigned long long)id << 8) | (unsigned long long)((-code) & 0xff);
+    atomicMin(err, key);
+}
+
+__device__ __forceinline__ bool has_error(const unsigned long long *err)
+{
+    return *((volatile const unsigned long long *)err) != ~0ULL;
+}
+
+// order-preserving map of doubles to unsigned 64-bit integers (for exact min/max atomics)
+__device__ __forceinline__ unsigned long long dkey(double v)
+{
+    unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ULL);
+}
+
+__device__ __forceinline__ double dkey_inv(unsigned long long k)
+{
+    unsigned long long b = (k >> 63) ? (k & 0x7FFFFFFFFFFFFFFFULL) : ~k;
+    return __longlong_as_double((long long)b);
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ float warp_sumf(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_max(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// linked-cell coordinate: floor((x - o) / c) in correctly rounded FP64 (bit-identical to any
+// IEEE implementation of the same expression), optionally clamped to the grid.
+__device__ __forceinline__ int cell_coord(double x, double o, double c, int n, bool clamp)
+{
+    double f = floor(__ddiv_rn(__dsub_rn(x, o), c));
+    if (clamp) {
+        f = fmin(fmax(f, 0.0), (double)(n - 1));
+    } else {
+        f = fmin(fmax(f, -4.0), (double)(n + 3));
+    }
+    return (int)f;
+}
+
+// |a - b|^2 with the fixed order ((dx*dx) + (dy*dy)) + (dz*dz) and no contraction
+__device__ __forceinline__ double dist2_exact(double ax, double ay, double az, double bx, double by,
+                                             double bz)
+{
+    double dx = __dsub_rn(ax, bx), dy = __dsub_rn(ay, by), dz = __dsub_rn(az, bz);
+    return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+// bitonic sort (ascending) of a[0..n2) in shared memory by one warp; n2 a power of two
+template <typename T>
+__device__ __forceinline__ void warp_bitonic_sort(T *a, int n2, int lane)
+{
+    for (int k = 2; k <= n2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = lane; i < n2; i += kWarp) {
+                int ixj = i ^ j;
+                if (ixj > i) {
+                    T ai = a[i], aj = a[ixj];
+                    bool up = ((i & k) == 0);
+                    if ((ai > aj) == up) {
+                        a[i] = aj;
+                        a[ixj] = ai;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+__host__ __device__ __forceinline__ int next_pow2(int v)
+{
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+// ------------------------------------------------------------------ host-side launchers
+// Each returns cudaGetLastError() of its launches; `launches` counts kernels enqueued.
+cudaError_t launch_grid_build(const Dev &D, cudaStream_t s, long long *launches);
+cudaError_t launch_search_lme(const Dev &D, bool init, cudaStream_t s, long long *launches);
+cudaError_t launch_node_major_impl(const Dev &D, int32_t *tmp, cudaStream_t s, long long *launches);
+cudaError_t launch_node_update(const Dev &D, double t_next, cudaStream_t s, long long *launches);
+cudaError_t launch_pack3to4(const double *x3, int64_t n, double4_32a *x4, cudaStream_t s, long long *launches);
+cudaError_t launch_init_state(const Dev &D, double T0, cudaStream_t s, long long *launches);
+cudaError_t launch_du_to_f32(const Dev &D, cudaStream_t s, long long *launches);
+cudaError_t launch_kinematics(const Dev &D, cudaStream_t s, long long *launches);
+cudaError_t launch_return_map(const Dev &D, cudaStream_t s, long long *launches);
+cudaError_t launch_exclusive_scan_tmp(const int32_t *in, int32_t *out, int64_t n, int32_t *tmp,
+                                      cudaStream_t s, long long *launches);
+size_t scan_tmp_ints(int64_t n);
+bool carve_search_scratch(void *base, size_t bytes, int64_t nn, SearchScratch *S);
+cudaError_t build_search_grid(const double *node_x, int64_t nn, double cell, SearchScratch *S,
+                              double *grid_out, cudaStream_t s);
+size_t search_lme_smem_bytes(int S, int warps);
+
+// stand-alone entry points reuse these
+cudaError_t launch_search_only(const double *node_x, int64_t nn, const double *mp_x, int64_t nm,
+                               double rs2, double cell, int S, int32_t *ids, int32_t *counts,
+                               void *scratch, size_t scratch_bytes, double *grid_out,
+                               int32_t *status, cudaStream_t s);
+size_t search_scratch_bytes(int64_t nn);
+cudaError_t launch_lme_only(const double *node_x, const double *mp_x, int64_t nm,
+                            const int32_t *ids, const int32_t *counts, int S, double beta,
+                            double tol_abs, int max_newton, double *lam, double *shape,
+                            int32_t *iters, int32_t *status, cudaStream_t s);
+cudaError_t launch_return_map_only(const otm_material *mat, double dt, int64_t nm, const double *dF,
+                                   const double *F_new, double *be, double *ebar, double *T,
+                                   double *sigma, double *rate, uint8_t *failed, int32_t *status,
+                                   cudaStream_t s);
+
+}  // namespace otm

@@ -1,0 +1,118 @@
+"""GPU parity of the whole explicit step (Algorithm 1) against the oracle, through the C ABI.
+
+FP64 path: neighbour lists bit-exact and every field within 1e-10 relative of the oracle
+(max |gpu - oracle| / max |oracle|) after a multi-step trajectory. Mixed path: errors per field
+against the FP64 oracle within stated bounds. Determinism: two runs bit-identical."""
+import numpy as np
+import pytest
+
+import scenarios
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FIELDS_NODE = ["node_x", "node_du"]
+FIELDS_MP = ["mp_x", "F", "sigma", "be", "vol", "ebar", "T", "lam"]
+
+
+def rel(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    s = np.abs(b).max()
+    return np.abs(a - b).max() / (s if s > 0 else 1.0)
+
+
+@pytest.fixture(scope="module")
+def OTM():
+    import paper_2206_08772_gb300 as g
+    g.load()
+    from paper_2206_08772_gb300.otm import OTM
+    return OTM
+
+
+def compare(sim_g, sim_o, fields_tol):
+    errs = {}
+    for f in FIELDS_NODE + FIELDS_MP:
+        g = sim_g.get(f)
+        o = sim_o.get(f)
+        errs[f] = rel(g, o)
+    bad = {f: e for f, e in errs.items() if e > fields_tol.get(f, fields_tol["default"])}
+    return errs, bad
+
+
+def supports_equal(sim_g, sim_o):
+    off_g, ids_g = sim_g.supports()
+    off_o, ids_o = sim_o.get("offsets"), sim_o.get("ids")
+    return np.array_equal(off_g, off_o) and np.array_equal(ids_g, ids_o)
+
+
+@pytest.mark.parametrize("name,steps", [("taylor_j2_short", 30), ("taylor_jc_short", 30)])
+def test_fp64_trajectory_matches_oracle(orc, OTM, name, steps):
+    mat = scenarios.copper_j2() if "j2" in name else scenarios.copper_jc()
+    p = scenarios.taylor_rod(h=0.8e-3, R=3.2e-3, L=9.6e-3, material=mat)
+    sim_o = orc.Sim(p)
+    sim_g = OTM(p, precision="fp64")
+    assert supports_equal(sim_g, sim_o)
+    for k in range(steps):
+        assert sim_o.step(1) == 0
+        assert sim_g.step(1) == 0, sim_g.error()
+        assert supports_equal(sim_g, sim_o), f"step {k + 1}"
+    errs, bad = compare(sim_g, sim_o, {"default": 1e-10})
+    print(name, errs)
+    assert not bad, bad
+    assert sim_o.get("ebar").max() > 0
+
+
+def test_fp64_config1_full_100_steps(orc, OTM):
+    """The plain Taylor rod (R 3.2 mm, L 25.4 mm, h 0.8 mm, J2, 100 steps)."""
+    p = scenarios.config_taylor_j2()
+    sim_o = orc.Sim(p)
+    sim_g = OTM(p, precision="fp64")
+    assert sim_g.step(p.steps) == 0, sim_g.error()
+    assert sim_o.step(p.steps) == 0
+    assert supports_equal(sim_g, sim_o)
+    errs, bad = compare(sim_g, sim_o, {"default": 1e-10})
+    print("config1", errs)
+    assert not bad, bad
+    m = sim_g.get("node_mass")
+    assert abs(m.sum() - p.mp_mass.sum()) <= 1e-12 * p.mp_mass.sum()
+
+
+def test_mixed_path_error_table(orc, OTM):
+    p = scenarios.taylor_rod(h=0.8e-3, R=3.2e-3, L=9.6e-3, material=scenarios.copper_jc())
+    sim_o = orc.Sim(p)
+    sim_g = OTM(p, precision="mixed")
+    steps = 30
+    assert sim_g.step(steps) == 0, sim_g.error()
+    assert sim_o.step(steps) == 0
+    errs, bad = compare(sim_g, sim_o, {"default": 1e-4, "node_x": 1e-7, "mp_x": 1e-7})
+    print("mixed", errs)
+    assert not bad, bad
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_determinism(OTM, precision):
+    p = scenarios.taylor_rod(h=0.8e-3, R=3.2e-3, L=6.4e-3, material=scenarios.copper_jc())
+    outs = []
+    for _ in range(2):
+        s = OTM(p, precision=precision)
+        assert s.step(10) == 0
+        outs.append([s.get(f).copy() for f in FIELDS_NODE + FIELDS_MP])
+        s.close()
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+
+
+def test_error_status_nonconvergence(OTM):
+    """A point far outside its support's hull makes the Newton solve fail: the step reports
+    OTM_ERR_LME_NOCONV with the point's ID, and the GPU stays usable."""
+    p = scenarios.taylor_rod(h=0.8e-3, R=3.2e-3, L=4.0e-3, wall=False)
+    s = OTM(p)
+    xp = s.get("mp_x")
+    xp[7] += np.array([5.0e-3, 0.0, 0.0])     # pushed radially out of the rod (R = 3.2 mm)
+    s.set("mp_x", xp)
+    st = s.refresh()
+    code, fid = s.error()
+    assert st == code
+    assert code in (-4, -8)
+    s2 = OTM(p)
+    assert s2.step(2) == 0
