@@ -1,0 +1,325 @@
+"""Benchmark of the explicit OTM material-point update on GB300.
+
+Workload (default): the scaled-up Johnson-Cook Taylor rod with adiabatic heating, R 3.2 mm,
+L 25.4 mm, h 0.12 mm: 501,189 nodes, 2,854,368 material points (synthetic, seeded). A step is one
+pass of Algorithm 1 over all points (node update, kinematics, return map, linked-cell search,
+LME shape functions, node-major lists). Metric: material-point-steps/s = n_mps * steps / time.
+
+value       : FP64 path, inputs resident in HBM, CUDA events on the library's stream.
+mixed       : the FP32-scatter / FP64-Newton path on the same workload.
+e2e         : the same metric through the C ABI with pinned host buffers: otm_init (H2D of the
+              problem + initial supports) + every step followed by a D2H of the node positions.
+roofline    : the search + LME kernel (the dominant kernel), FP64-ALU bound.
+cpu_baseline: the serial FP64 oracle on a bounded sample of the same workload (a contiguous
+              block of material points in the middle of the rod, with the full node set).
+
+--gpus N under torchrun: N independent replicas (one rod per GPU, no collective in the data
+path; "scaling": "weak"); the timing is bracketed by barriers and the max over ranks is taken.
+--impl reference: times the oracle (the CPU reference) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import scenarios  # noqa: E402
+
+METRIC = "material-point-steps/s on 1 GB300 (FP64 vs mixed); adjoint/forward time ratio"
+UNIT = "MP-steps/s"
+
+# FP64 arithmetic executed by the search + LME kernel per material point and step, counted
+# from the algorithm: candidates * 8 + pairs * (29 per Newton evaluation + 45 final)
+FP64_PER_CAND = 8
+FP64_PER_PAIR_EVAL = 29
+FP64_PER_PAIR_FINAL = 45
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 2 FP64 FMA lanes / SM / clock at 2070 MHz
+
+
+def workload(name: str, seed: int = 0):
+    if name == "taylor_jc_h0.12":
+        return scenarios.config_taylor_jc(h=0.12e-3, seed=seed)
+    if name == "taylor_jc_h0.29":
+        return scenarios.taylor_rod(h=0.29e-3, material=scenarios.copper_jc(), seed=seed,
+                                    name="taylor_jc_h0.29")
+    if name == "taylor_j2_h0.8":
+        return scenarios.config_taylor_j2(seed=seed)
+    raise ValueError(name)
+
+
+def cpu_sample(prob, layers: int = 4):
+    """A bounded sample of the workload for the oracle: the material points of `layers` cell
+    layers in the middle of the rod (complete supports), with the full node set."""
+    per_layer = prob.n_mps // int(round(prob.meta["L"] / prob.h))
+    k0 = int(round(prob.meta["L"] / prob.h)) // 2
+    sl = slice(k0 * per_layer, (k0 + layers) * per_layer)
+    import copy
+    s = copy.copy(prob)
+    s.mp_x = prob.mp_x[sl].copy()
+    s.mp_vol = prob.mp_vol[sl].copy()
+    s.mp_mass = prob.mp_mass[sl].copy()
+    s.mp_material = prob.mp_material[sl].copy()
+    return s
+
+
+# ---------------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples (SM clock, throttle reasons) taken during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm_, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm_)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------- GPU arm
+def time_gpu(prob, precision, steps, warmup, torch, dist):
+    from paper_2206_08772_gb300.otm import OTM
+    sim = OTM(prob, precision=precision)
+    stream = sim.stream
+    for _ in range(warmup):
+        st = sim.step(1)
+        if st != 0:
+            raise RuntimeError(f"warm-up step failed: {st} {sim.error()}")
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = sim.launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    st = sim.step(steps, sync=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    code, fid = sim.error()
+    if st != 0 or code != 0:
+        raise RuntimeError(f"timed steps failed: {st} {code} {fid}")
+    launches = sim.launches() - l0
+    cnt = sim.get("support_count").astype(np.float64)
+    it = sim.get("newton_it").astype(np.float64)
+    info = dict(ms=ms, launches=launches, mean_support=float(cnt.mean()), mean_newton_it=float(it.mean()))
+    return sim, info
+
+
+def phase_profile(sim, steps: int = 3):
+    """Per-phase average milliseconds (CUDA events around each phase on the library stream)."""
+    sim.phase_times()
+    sim.phase_timing(True)
+    st = sim.step(steps)
+    pt = sim.phase_times()
+    sim.phase_timing(False)
+    if st != 0:
+        raise RuntimeError(f"profiled steps failed: {st}")
+    return {k: (ms / n if n else 0.0) for k, (ms, n) in pt.items()}
+
+
+def time_e2e(prob, precision, steps, torch):
+    """Through the C ABI with pinned host buffers: H2D of the problem inside otm_init, then per
+    step otm_step + a D2H read of the node positions."""
+    from paper_2206_08772_gb300.otm import OTM
+
+    def pinned(a):
+        t = torch.empty(a.shape, dtype=getattr(torch, str(a.dtype)), pin_memory=True)
+        t.numpy()[...] = a
+        return t.numpy()
+
+    host = dict(node_x=pinned(prob.node_x), node_du0=pinned(prob.node_du0),
+                node_flags=pinned(prob.node_flags), mp_x=pinned(prob.mp_x), mp_vol=pinned(prob.mp_vol),
+                mp_mass=pinned(prob.mp_mass), mp_material=pinned(prob.mp_material.astype(np.int32)))
+    out = pinned(np.zeros((prob.n_nodes, 3)))
+    h2d = sum(v.nbytes for v in host.values())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim = OTM(prob, precision=precision, host_arrays=host)
+    for _ in range(steps):
+        st = sim.step(1, sync=False)
+        if st != 0:
+            raise RuntimeError(f"e2e step failed {st}")
+        sim.get("node_x", out=out)
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    sim.close()
+    return dict(value=prob.n_mps * steps / t, unit=UNIT, h2d_bytes_per_step=int(h2d // max(steps, 1)),
+                d2h_bytes_per_step=int(out.nbytes), seconds=t)
+
+
+def time_oracle(prob, steps: int, warmup: int = 0):
+    import oracle
+    samp = cpu_sample(prob)
+    t0 = time.perf_counter()
+    sim = oracle.Sim(samp)
+    t_init = time.perf_counter() - t0
+    for _ in range(warmup):
+        sim.step(1)
+    t0 = time.perf_counter()
+    st = sim.step(steps)
+    t = time.perf_counter() - t0
+    if st != 0:
+        raise RuntimeError(f"oracle step failed {st}")
+    return dict(value=samp.n_mps * steps / t, unit=UNIT, cores=1, kind="oracle",
+                sample=(f"{samp.n_mps} MPs (4 cell layers at mid-length) of the {prob.n_mps}-MP rod with all "
+                        f"{prob.n_nodes} nodes, {steps} oracle steps after init ({t_init:.1f} s); serial C, 1 thread"),
+                seconds=t)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="taylor_jc_h0.12")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    prob = workload(args.workload)
+    config = {"workload": f"{prob.name}: Taylor rod R 3.2 mm, L 25.4 mm, Johnson-Cook copper + adiabatic heating",
+              "n_nodes": prob.n_nodes, "n_mps": prob.n_mps, "h_mm": prob.h * 1e3, "gamma": prob.gamma,
+              "support_tol": prob.support_tol, "dt_s": prob.dt, "max_support": 384,
+              "l2": "inputs larger than L2 (pair arrays of tens of GB)", "parallelism": f"replicas x{args.gpus}"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        o = time_oracle(prob, args.steps, args.warmup)
+        line = {"impl": "reference", "metric": METRIC, "value": o["value"], "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * o["seconds"] / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": config,
+                "cpu_baseline": {"value": o["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                                 "sample": o["sample"]},
+                "e2e": {"value": o["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_
+        torch.cuda.set_device(local)
+        dist_.init_process_group("nccl")
+        dist = dist_
+    else:
+        torch.cuda.set_device(0)
+
+    with ClockSampler(local) as clk:
+        sim, info = time_gpu(prob, "fp64", args.steps, args.warmup, torch, dist)
+    phases = phase_profile(sim)
+    k_ms = phases["search_lme"]
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+    ms_t = torch.tensor([info["ms"]], device="cuda")
+    if dist is not None:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms = float(ms_t.item())
+    value = world * prob.n_mps * args.steps / (ms / 1e3)
+
+    mixed = None
+    if not args.no_mixed:
+        simm, infom = time_gpu(prob, "mixed", args.steps, args.warmup, torch, dist)
+        simm.close()
+        del simm
+        torch.cuda.empty_cache()
+        mv = world * prob.n_mps * args.steps / (infom["ms"] / 1e3)
+        mixed = {"value": mv, "unit": UNIT, "ms_per_step": infom["ms"] / args.steps,
+                 "speedup_vs_fp64": mv / value, "dtype": "f32 scatter/node update, f64 elsewhere"}
+    e2e = None
+    if not args.no_e2e:
+        e2e = time_e2e(prob, "fp64", args.steps, torch)
+        e2e["value"] *= world
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    n_bar, k_bar = info["mean_support"], info["mean_newton_it"]
+    cand = 3.73 * n_bar            # (5 cells)^3 of edge r_s/2 vs the support sphere
+    flops_mp = FP64_PER_CAND * cand + n_bar * (FP64_PER_PAIR_EVAL * (k_bar + 1) + FP64_PER_PAIR_FINAL)
+    achieved = flops_mp * prob.n_mps / (k_ms / 1e3) / 1e12
+    roofline = {"kernel": "k_search_lme (+ grid build and node-major lists, steps 5-6)", "bound": "alu",
+                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz (probe measured 1.20)",
+                "algorithmic_fp64_flops_per_mp": flops_mp, "kernel_ms": k_ms}
+    cpu = None
+    if not args.no_cpu_baseline:
+        o = time_oracle(prob, 2)
+        cpu = {k: o[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
+            "gpu_launches": info["launches"], "mixed": mixed, "e2e": e2e, "roofline": roofline,
+            "cpu_baseline": cpu, "clocks": clk.summary(),
+            "stats": {"mean_support": n_bar, "mean_newton_iterations": k_bar},
+            "phases_ms": phases}
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -148,6 +148,21 @@ int otm_error_detail(otm_handle *h, int32_t *code, int64_t *first_id);
 /* Launch statistics: kernels enqueued since otm_init. */
 int otm_kernel_launches(otm_handle *h, int64_t *launches);
 
+/* Phase timing: with timing on, every phase of a step is bracketed by CUDA events on the
+ * library's stream. otm_phase_times synchronises, returns the summed milliseconds and the
+ * number of timed launches of each phase since the previous call, and resets them. */
+enum {
+    OTM_PHASE_NODE_UPDATE = 0,   /* Eq. 4-6: segmented reduction, central difference, contact */
+    OTM_PHASE_KINEMATICS = 1,    /* Eq. 9-13 */
+    OTM_PHASE_RETURN_MAP = 2,    /* Sec. 4.1 / 4.2 */
+    OTM_PHASE_GRID = 3,          /* Algorithm 3 step 1: linked-cell counting sort */
+    OTM_PHASE_SEARCH_LME = 4,    /* Algorithm 3 steps 2-3 + Eq. 14 + contributions */
+    OTM_PHASE_NODE_MAJOR = 5,    /* influence lists: scan + fill */
+    OTM_N_PHASES = 6
+};
+int otm_phase_timing(otm_handle *h, int32_t enable);
+int otm_phase_times(otm_handle *h, double *ms, int64_t *launches);
+
 void otm_destroy(otm_handle *h);
 
 /* ---------------------------------------------------------------------------------------

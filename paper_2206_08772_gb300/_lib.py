@@ -22,6 +22,8 @@ ERR_NAMES = {0: "OK", -1: "ARG", -2: "CUDA", -3: "WORKSPACE", -4: "LME_NOCONV", 
 
 PRECISION_FP64, PRECISION_MIXED = 0, 1
 
+PHASES = ["node_update", "kinematics", "return_map", "grid", "search_lme", "node_major"]
+
 FIELD = dict(node_x=0, node_du=1, node_mass=2, node_force=3, mp_x=4, F=5, be=6, sigma=7, vol=8,
              ebar=9, T=10, lam=11, support_count=12, support_ids=13, shape=14, newton_it=15,
              rate=16, dF=17, mp_gid=18, node_gid=19, node_flags=20)
@@ -80,6 +82,8 @@ _SIGS = {
     "otm_error_detail": (C.c_int, [_P, _P, _P]),
     "otm_kernel_launches": (C.c_int, [_P, _P]),
     "otm_destroy": (None, [_P]),
+    "otm_phase_timing": (C.c_int, [_P, _I32]),
+    "otm_phase_times": (C.c_int, [_P, _P, _P]),
     "otm_search_scratch_bytes": (C.c_int, [_I64, _P]),
     "otm_support_search": (C.c_int, [_P, _I64, _P, _I64, _D, _D, _I32, _P, _P, _P, _SZ, _P, _P, _P]),
     "otm_lme": (C.c_int, [_P, _P, _I64, _P, _P, _I32, _D, _D, _I32, _P, _P, _P, _P, _P]),

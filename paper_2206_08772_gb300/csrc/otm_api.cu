@@ -3,6 +3,10 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <vector>
+
+#include <new>
+
 #include "otm_dev.cuh"
 
 using namespace otm;
@@ -16,6 +20,34 @@ struct otm_handle {
     int32_t *scan_tmp;
     int64_t step;
     long long launches;
+    // phase timing
+    bool timing;
+    struct Rec {
+        int phase;
+        cudaEvent_t a, b;
+    };
+    std::vector<Rec> recs;
+    double phase_ms[OTM_N_PHASES];
+    int64_t phase_n[OTM_N_PHASES];
+};
+
+// bracket one phase with events when timing is on
+struct PhaseScope {
+    otm_handle *h;
+    int phase;
+    cudaEvent_t a = nullptr, b = nullptr;
+    PhaseScope(otm_handle *h_, int ph) : h(h_), phase(ph)
+    {
+        if (h->timing && cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess)
+            cudaEventRecord(a, h->stream);
+    }
+    ~PhaseScope()
+    {
+        if (h->timing && a && b) {
+            cudaEventRecord(b, h->stream);
+            h->recs.push_back({phase, a, b});
+        }
+    }
 };
 
 #define CK(call)                                  \
@@ -171,11 +203,20 @@ static int rebuild_supports(otm_handle *h)
 {
     Dev &D = h->D;
     cudaStream_t s = h->stream;
-    CK(launch_grid_build(D, s, &h->launches));
+    {
+        PhaseScope ps(h, OTM_PHASE_GRID);
+        CK(launch_grid_build(D, s, &h->launches));
+    }
     CK(cudaMemsetAsync(D.ncount, 0, (size_t)D.nn * sizeof(int32_t), s));
     CK(cudaMemsetAsync(D.emax, 0x80, 2 * sizeof(int), s));
-    CK(launch_search_lme(D, false, s, &h->launches));
-    CK(launch_node_major_impl(D, h->scan_tmp, s, &h->launches));
+    {
+        PhaseScope ps(h, OTM_PHASE_SEARCH_LME);
+        CK(launch_search_lme(D, false, s, &h->launches));
+    }
+    {
+        PhaseScope ps(h, OTM_PHASE_NODE_MAJOR);
+        CK(launch_node_major_impl(D, h->scan_tmp, s, &h->launches));
+    }
     return OTM_OK;
 }
 
@@ -196,7 +237,7 @@ extern "C" int otm_init(const otm_problem *prob, const otm_params *params, void 
     size_t need = layout(nn, nm, params->max_support, params->precision, nullptr, nullptr, nullptr);
     if (ws_bytes < need) return OTM_ERR_WORKSPACE;
 
-    otm_handle *h = (otm_handle *)calloc(1, sizeof(otm_handle));
+    otm_handle *h = new (std::nothrow) otm_handle();
     if (!h) return OTM_ERR_ARG;
     h->P = *params;
     h->stream = (cudaStream_t)stream;
@@ -236,7 +277,7 @@ extern "C" int otm_init(const otm_problem *prob, const otm_params *params, void 
         rc = read_error(h, nullptr, nullptr);
     } while (0);
     if (rc != OTM_OK) {
-        free(h);
+        delete h;
         return rc;
     }
     *out = h;
@@ -248,12 +289,18 @@ static int enqueue_step(otm_handle *h)
     Dev &D = h->D;
     cudaStream_t s = h->stream;
     const double t_next = (double)(h->step + 1) * D.dt;
-    // 1-2: lumped mass / force (segmented reduction), central difference, contact, x update
-    CK(launch_node_update(D, t_next, s, &h->launches));
-    // 3: MP position, F, volume
-    CK(launch_kinematics(D, s, &h->launches));
-    // 4: constitutive update
-    CK(launch_return_map(D, s, &h->launches));
+    {   // 1-2: lumped mass / force (segmented reduction), central difference, contact, x update
+        PhaseScope ps(h, OTM_PHASE_NODE_UPDATE);
+        CK(launch_node_update(D, t_next, s, &h->launches));
+    }
+    {   // 3: MP position, F, volume
+        PhaseScope ps(h, OTM_PHASE_KINEMATICS);
+        CK(launch_kinematics(D, s, &h->launches));
+    }
+    {   // 4: constitutive update
+        PhaseScope ps(h, OTM_PHASE_RETURN_MAP);
+        CK(launch_return_map(D, s, &h->launches));
+    }
     // 5-6: linked-cell search, LME shape functions, contributions, node-major lists
     int rc = rebuild_supports(h);
     if (rc != OTM_OK) return rc;
@@ -397,11 +444,45 @@ extern "C" int otm_refresh(otm_handle *h)
     return read_error(h, nullptr, nullptr);
 }
 
+extern "C" int otm_phase_timing(otm_handle *h, int32_t enable)
+{
+    if (!h) return OTM_ERR_ARG;
+    h->timing = enable != 0;
+    return OTM_OK;
+}
+
+extern "C" int otm_phase_times(otm_handle *h, double *ms, int64_t *launches)
+{
+    if (!h) return OTM_ERR_ARG;
+    CK(cudaStreamSynchronize(h->stream));
+    for (auto &r : h->recs) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+            h->phase_ms[r.phase] += t;
+            h->phase_n[r.phase] += 1;
+        }
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    h->recs.clear();
+    for (int i = 0; i < OTM_N_PHASES; i++) {
+        if (ms) ms[i] = h->phase_ms[i];
+        if (launches) launches[i] = h->phase_n[i];
+        h->phase_ms[i] = 0.0;
+        h->phase_n[i] = 0;
+    }
+    return OTM_OK;
+}
+
 extern "C" void otm_destroy(otm_handle *h)
 {
     if (!h) return;
     cudaStreamSynchronize(h->stream);
-    free(h);
+    for (auto &r : h->recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    delete h;
 }
 
 // ------------------------------------------------------------------ stand-alone entries

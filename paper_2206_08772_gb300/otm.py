@@ -128,6 +128,16 @@ class OTM:
         check(_lib.load().otm_kernel_launches(self._h, C.byref(v)), "otm_kernel_launches")
         return v.value
 
+    def phase_timing(self, on: bool = True):
+        check(_lib.load().otm_phase_timing(self._h, 1 if on else 0), "otm_phase_timing")
+
+    def phase_times(self) -> dict:
+        """{phase: (total ms, launches)} since the previous call (synchronises)."""
+        ms = (C.c_double * len(_lib.PHASES))()
+        n = (C.c_int64 * len(_lib.PHASES))()
+        check(_lib.load().otm_phase_times(self._h, ms, n), "otm_phase_times")
+        return {k: (ms[i], n[i]) for i, k in enumerate(_lib.PHASES)}
+
     def refresh(self) -> int:
         return _lib.load().otm_refresh(self._h)
 
