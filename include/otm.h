@@ -184,6 +184,23 @@ int otm_support_search(const double *node_x, int64_t n_nodes, const double *mp_x
                        int32_t *counts, void *scratch, size_t scratch_bytes, double *grid_out,
                        int32_t *status, void *stream);
 
+/* Allocation-free variant of otm_support_search, for callers that cannot allocate device
+ * memory when they call (for instance a process whose device memory is already reserved by
+ * another allocator, or a loop that must not take cudaMalloc's implicit synchronisation).
+ * The paper has no counterpart: this is a deployment convenience, not part of the method.
+ * Same arguments, outputs and status as otm_support_search minus the scratch buffer: the
+ * scratch is a static 14 MiB device array inside the library, held by every GPU that loads it
+ * until the process exits. n_nodes must be <= OTM_NOALLOC_MAX_NODES (else OTM_ERR_CAPACITY,
+ * nothing launched). The first call on a device looks up that array's device address with the
+ * device current (call it once before any stream capture). All calls share the one array and
+ * it keeps the previous call's contents (every call re-initialises what it reads), so calls
+ * whose work overlaps on the GPU -- on different streams or from different threads without
+ * ordering -- race; serialise them on one stream. Allocates nothing. */
+#define OTM_NOALLOC_MAX_NODES 65536
+int otm_support_search_noalloc(const double *node_x, int64_t n_nodes, const double *mp_x, int64_t n_mps,
+                               double rs2, double cell_size, int32_t max_support, int32_t *ids,
+                               int32_t *counts, double *grid_out, int32_t *status, void *stream);
+
 /* LME shape functions (Eq. 14) for n_mps points with given supports (ids/counts as produced
  * by otm_support_search). lambda (n_mps x 3, in: start, out: solution). shape: n_mps x
  * max_support x 4 doubles (N, dN/dx, dN/dy, dN/dz). iters (n_mps, optional). status: as above
