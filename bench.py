@@ -9,7 +9,7 @@ value       : FP64 path, inputs resident in HBM, CUDA events on the library's st
 mixed       : the FP32-scatter / FP64-Newton path on the same workload.
 e2e         : the same metric through the C ABI with pinned host buffers: otm_init (H2D of the
               problem + initial supports) + every step followed by a D2H of the node positions.
-roofline    : the search + LME kernel (the dominant kernel), FP64-ALU bound.
+roofline    : the dominant kernel of the step (largest phase time) against its ALU peak.
 cpu_baseline: the serial FP64 oracle on a bounded sample of the same workload (a contiguous
               block of material points in the middle of the rod, with the full node set).
 
@@ -38,12 +38,17 @@ import scenarios  # noqa: E402
 METRIC = "material-point-steps/s on 1 GB300 (FP64 vs mixed); adjoint/forward time ratio"
 UNIT = "MP-steps/s"
 
-# FP64 arithmetic executed by the search + LME kernel per material point and step, counted
-# from the algorithm: candidates * 8 + pairs * (29 per Newton evaluation + 45 final)
-FP64_PER_CAND = 8
-FP64_PER_PAIR_EVAL = 29
-FP64_PER_PAIR_FINAL = 45
+# Algorithmic arithmetic per unit (an FMA counts 2 flops), counted from the kernels' algorithms:
+#  k_lme (FP64): per pair 8 (d, prior exponent) + 44 per Newton evaluation (exponent 7, the
+#  table-driven exp 18, Z / r / J accumulation 19) + 39 final (N, grad N = -N J^-1 d, mass and
+#  force contributions); evaluations = 1 + Newton iterations.
+#  k_search (FP32): 8 flops per candidate (3 sub, 1 mul, 2 fma); candidates ~ 3.73 x support.
+#  k_kinematics (FP64): 24 flops per pair (x_p: 3 fma, dF: 9 fma).
+LME_PER_PAIR_SETUP, LME_PER_PAIR_EVAL, LME_PER_PAIR_FINAL = 8, 44, 39
+SEARCH_PER_CAND, CAND_PER_PAIR = 8, 3.73
+KIN_PER_PAIR = 24
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 2 FP64 FMA lanes / SM / clock at 2070 MHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
 
 def workload(name: str, seed: int = 0):
@@ -268,7 +273,6 @@ def main():
     with ClockSampler(local) as clk:
         sim, info = time_gpu(prob, "fp64", args.steps, args.warmup, torch, dist)
     phases = phase_profile(sim)
-    k_ms = phases["search_lme"]
     sim.close()
     del sim
     torch.cuda.empty_cache()
@@ -297,14 +301,25 @@ def main():
         return
 
     n_bar, k_bar = info["mean_support"], info["mean_newton_it"]
-    cand = 3.73 * n_bar            # (5 cells)^3 of edge r_s/2 vs the support sphere
-    flops_mp = FP64_PER_CAND * cand + n_bar * (FP64_PER_PAIR_EVAL * (k_bar + 1) + FP64_PER_PAIR_FINAL)
-    achieved = flops_mp * prob.n_mps / (k_ms / 1e3) / 1e12
-    roofline = {"kernel": "k_search_lme (+ grid build and node-major lists, steps 5-6)", "bound": "alu",
-                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz (probe measured 1.20)",
-                "algorithmic_fp64_flops_per_mp": flops_mp, "kernel_ms": k_ms}
+    pairs = n_bar * prob.n_mps
+    work = {   # kernel -> (algorithmic TFLOP per launch, peak, bound)
+        "lme": (pairs * (LME_PER_PAIR_SETUP + LME_PER_PAIR_EVAL * (1 + k_bar) + LME_PER_PAIR_FINAL) / 1e12,
+                FP64_PEAK_TFLOPS, "fp64"),
+        "search": (pairs * CAND_PER_PAIR * SEARCH_PER_CAND / 1e12, FP32_PEAK_TFLOPS, "fp32"),
+        "kinematics": (pairs * KIN_PER_PAIR / 1e12, FP64_PEAK_TFLOPS, "fp64"),
+    }
+    kernels = {}
+    for k, (tf, peak, kind) in work.items():
+        ms_k = phases[k]
+        kernels[k] = {"ms": ms_k, "achieved_tflops": tf / (ms_k / 1e3), "peak": peak, "kind": kind,
+                      "frac": tf / (ms_k / 1e3) / peak}
+    dom = max(kernels, key=lambda k: kernels[k]["ms"])
+    kd = kernels[dom]
+    roofline = {"kernel": f"k_{dom}", "bound": "alu", "achieved": kd["achieved_tflops"], "peak": kd["peak"],
+                "unit": "TFLOP/s", "frac": kd["frac"], "traffic": None,
+                "peak_source": ("derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz (probe measured 1.20)"
+                                if kd["kind"] == "fp64" else "derived: 152 SMs x 128 FP32 FMA/clk x 2 x 2070 MHz"),
+                "kernel_ms": kd["ms"], "share_of_step": kd["ms"] / (ms / args.steps), "kernels": kernels}
     cpu = None
     if not args.no_cpu_baseline:
         o = time_oracle(prob, 2)

@@ -156,9 +156,10 @@ enum {
     OTM_PHASE_KINEMATICS = 1,    /* Eq. 9-13 */
     OTM_PHASE_RETURN_MAP = 2,    /* Sec. 4.1 / 4.2 */
     OTM_PHASE_GRID = 3,          /* Algorithm 3 step 1: linked-cell counting sort */
-    OTM_PHASE_SEARCH_LME = 4,    /* Algorithm 3 steps 2-3 + Eq. 14 + contributions */
-    OTM_PHASE_NODE_MAJOR = 5,    /* influence lists: scan + fill */
-    OTM_N_PHASES = 6
+    OTM_PHASE_SEARCH = 4,        /* Algorithm 3 steps 2-3: supports, influence counts */
+    OTM_PHASE_NODE_MAJOR = 5,    /* influence-list offsets (scan of the counts) */
+    OTM_PHASE_LME = 6,           /* Eq. 14 + per-pair contributions in node-major order */
+    OTM_N_PHASES = 7
 };
 int otm_phase_timing(otm_handle *h, int32_t enable);
 int otm_phase_times(otm_handle *h, double *ms, int64_t *launches);
@@ -189,7 +190,7 @@ int otm_support_search(const double *node_x, int64_t n_nodes, const double *mp_x
  * another allocator, or a loop that must not take cudaMalloc's implicit synchronisation).
  * The paper has no counterpart: this is a deployment convenience, not part of the method.
  * Same arguments, outputs and status as otm_support_search minus the scratch buffer: the
- * scratch is a static 14 MiB device array inside the library, held by every GPU that loads it
+ * scratch is a static 16 MiB device array inside the library, held by every GPU that loads it
  * until the process exits. n_nodes must be <= OTM_NOALLOC_MAX_NODES (else OTM_ERR_CAPACITY,
  * nothing launched). The first call on a device looks up that array's device address with the
  * device current (call it once before any stream capture). All calls share the one array and
@@ -209,6 +210,10 @@ int otm_lme(const double *node_x, const double *mp_x, int64_t n_mps, const int32
             const int32_t *counts, int32_t max_support, double beta, double tol_abs,
             int32_t max_newton, double *lambda, double *shape, int32_t *iters, int32_t *status,
             void *stream);
+
+/* Self-test of the library's internal FP64 exponential (Tang's table-driven method, used for
+ * the LME weights of Eq. 14): mine[i] = internal exp(x[i]), ref[i] = CUDA's exp(x[i]). */
+int otm_exp_selftest(const double *x, int64_t n, double *mine, double *ref, void *stream);
 
 /* Constitutive update (Sec. 4.1 / 4.2) of n_mps points: inputs dF (9), F_new (9, for J),
  * be (6, in/out), ebar, T (in/out); outputs sigma (6), rate, failed (uint8, optional). */

@@ -3,6 +3,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
+#include <numeric>
 #include <vector>
 
 #include <new>
@@ -81,6 +83,7 @@ static size_t layout(int64_t nn, int64_t nm, int S, int precision, char *base, D
     TAKE(d.du, double4_32a, nn);
     TAKE(d.mr, double4_32a, nn);
     TAKE(d.spos, double4_32a, nn);
+    TAKE(d.spos32, float4, nn);
     TAKE(d.du32, float4, nn);
     TAKE(d.nflags, uint8_t, nn);
     TAKE(d.ngid, int64_t, nn);
@@ -103,8 +106,8 @@ static size_t layout(int64_t nn, int64_t nm, int S, int precision, char *base, D
     TAKE(d.ebar, double, nm);
     TAKE(d.T, double, nm);
     TAKE(d.rate, double, nm);
-    TAKE(d.Jdet, double, nm);
     TAKE(d.lam, double, 3 * nm);
+    TAKE(d.logz, double, nm);
     TAKE(d.mat_id, int32_t, nm);
     TAKE(d.cnt, int32_t, nm);
     TAKE(d.newton_it, int32_t, nm);
@@ -119,7 +122,6 @@ static size_t layout(int64_t nn, int64_t nm, int S, int precision, char *base, D
         TAKE(d.contrib64, double4_32a, slots);
     }
     TAKE(d.rank, uint16_t, slots);
-    TAKE(d.perm, uint32_t, slots);
 #undef TAKE
     if (base) {
         d.nn = nn;
@@ -210,12 +212,16 @@ static int rebuild_supports(otm_handle *h)
     CK(cudaMemsetAsync(D.ncount, 0, (size_t)D.nn * sizeof(int32_t), s));
     CK(cudaMemsetAsync(D.emax, 0x80, 2 * sizeof(int), s));
     {
-        PhaseScope ps(h, OTM_PHASE_SEARCH_LME);
-        CK(launch_search_lme(D, false, s, &h->launches));
+        PhaseScope ps(h, OTM_PHASE_SEARCH);
+        CK(launch_search(D, s, &h->launches));
     }
     {
         PhaseScope ps(h, OTM_PHASE_NODE_MAJOR);
-        CK(launch_node_major_impl(D, h->scan_tmp, s, &h->launches));
+        CK(launch_node_offsets(D, h->scan_tmp, s, &h->launches));
+    }
+    {
+        PhaseScope ps(h, OTM_PHASE_LME);
+        CK(launch_lme(D, s, &h->launches));
     }
     return OTM_OK;
 }
@@ -409,6 +415,32 @@ extern "C" int otm_state(otm_handle *h, int32_t field, void *host_dst, size_t by
         CK(cudaMemcpy2DAsync(host_dst, v.width, v.src, v.pitch, v.width, v.rows, cudaMemcpyDeviceToHost,
                              h->stream));
     CK(cudaStreamSynchronize(h->stream));
+    if (field == OTM_FIELD_SUPPORT_IDS || field == OTM_FIELD_SHAPE) {
+        // rows are stored in linked-cell order; the export orders each row by node ID
+        const size_t nm = (size_t)h->D.nm, S = (size_t)h->D.S;
+        std::vector<int32_t> cnt(nm), ids;
+        CK(cudaMemcpy(cnt.data(), h->D.cnt, nm * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        if (field == OTM_FIELD_SUPPORT_IDS) {
+            int32_t *row = (int32_t *)host_dst;
+            for (size_t p = 0; p < nm; p++) std::sort(row + p * S, row + p * S + cnt[p]);
+        } else {
+            ids.resize(nm * S);
+            CK(cudaMemcpy(ids.data(), h->D.ids, nm * S * sizeof(int32_t), cudaMemcpyDeviceToHost));
+            double *sh = (double *)host_dst;
+            std::vector<int> perm;
+            std::vector<double> tmp;
+            for (size_t p = 0; p < nm; p++) {
+                const int n = cnt[p];
+                perm.resize(n);
+                std::iota(perm.begin(), perm.end(), 0);
+                const int32_t *r = ids.data() + p * S;
+                std::sort(perm.begin(), perm.end(), [r](int a, int b) { return r[a] < r[b]; });
+                tmp.assign(sh + 4 * p * S, sh + 4 * (p * S + n));
+                for (int k = 0; k < n; k++)
+                    for (int c = 0; c < 4; c++) sh[4 * (p * S + k) + c] = tmp[4 * perm[k] + c];
+            }
+        }
+    }
     return OTM_OK;
 }
 
@@ -516,6 +548,13 @@ extern "C" int otm_lme(const double *node_x, const double *mp_x, int64_t n_mps, 
     if (max_support < 1 || max_support > kMaxS || !(beta > 0) || !(tol_abs > 0)) return OTM_ERR_ARG;
     CK(launch_lme_only(node_x, mp_x, n_mps, ids, counts, max_support, beta, tol_abs, max_newton, lambda, shape,
                        iters, status, (cudaStream_t)stream));
+    return OTM_OK;
+}
+
+extern "C" int otm_exp_selftest(const double *x, int64_t n, double *mine, double *ref, void *stream)
+{
+    if (!x || !mine || !ref || n < 0) return OTM_ERR_ARG;
+    CK(launch_exp_selftest(x, n, mine, ref, (cudaStream_t)stream));
     return OTM_OK;
 }
 

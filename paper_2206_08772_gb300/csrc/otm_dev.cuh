@@ -6,8 +6,8 @@
 //   MPs    : x_p (double4_32a), F, dF (9), b^e, sigma (6), vol, mass, ebar, T, rate, J, lambda (3),
 //            material, support count, Newton iterations, failure flag, original ID
 //   pairs  : padded MP-major rows of S slots: node ID (int32), shape (double4_32a: N, grad N),
-//            contribution (double4_32a or float4: m_p N, -v sigma grad N), rank in node list
-//            (uint16), and the node-major permutation of slot indices (uint32)
+//            rank in the node's influence list (uint16); node-major contributions
+//            (double4_32a or float4: m_p N, -v sigma grad N) at noff[node] + rank
 #pragma once
 
 #include <cuda_runtime.h>
@@ -53,20 +53,20 @@ struct Dev {
     // linked cell
     GridDev *grid;
     int32_t *cell_count, *cell_start, *node_cell, *node_rank, *sorted;
-    double4_32a *spos;                   // node positions in (cell, ID) order, w = ID bits
+    double4_32a *spos;               // node positions in (cell, ID) order, w = ID bits
+    float4 *spos32;                  // the same relative to the grid origin in FP32, w = ID bits
     // material points
     double4_32a *xp;
-    double *F, *dF, *be, *sig, *vol, *mass, *ebar, *T, *rate, *Jdet, *lam;
+    double *F, *dF, *be, *sig, *vol, *mass, *ebar, *T, *rate, *lam, *logz;
     int32_t *mat_id, *cnt, *newton_it;
     uint8_t *failed;
     int64_t *mgid;
-    // pairs
+    // pairs: MP-major padded rows (ids, shape, rank) and node-major contributions
     int32_t *ids;
     double4_32a *shape;
     double4_32a *contrib64;
     float4 *contrib32;
     uint16_t *rank;
-    uint32_t *perm;
     // status: (first offending id << 8) | (-code), atomicMin
     unsigned long long *err;
     int *emax;                       // largest binary exponent of the mass / force terms (2 ints)
@@ -76,6 +76,7 @@ struct Dev {
 struct SearchScratch {
     GridDev *g;
     double4_32a *x4, *spos;
+    float4 *spos32;
     int32_t *cell_count, *cell_start, *node_cell, *node_rank, *sorted;
     unsigned long long *err;
     int max_cells;
@@ -118,6 +119,37 @@ __device__ __forceinline__ float warp_sumf(float v)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
+}
+
+// Reduce-scatter of 16 per-lane values over a warp in 16 additions per lane (instead of 5 per
+// value): after it, lanes 2j and 2j+1 hold the warp total of value j. Unused values may be 0.
+__device__ __forceinline__ double warp_reduce_scatter16(const double (&v)[16], int lane)
+{
+    double a[8], b[4], c[2], d;
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        const bool up = lane & 16;
+        const double mine = up ? v[8 + i] : v[i], other = up ? v[i] : v[8 + i];
+        a[i] = mine + __shfl_xor_sync(0xffffffffu, other, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        const bool up = lane & 8;
+        const double mine = up ? a[4 + i] : a[i], other = up ? a[i] : a[4 + i];
+        b[i] = mine + __shfl_xor_sync(0xffffffffu, other, 8);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; i++) {
+        const bool up = lane & 4;
+        const double mine = up ? b[2 + i] : b[i], other = up ? b[i] : b[2 + i];
+        c[i] = mine + __shfl_xor_sync(0xffffffffu, other, 4);
+    }
+    {
+        const bool up = lane & 2;
+        const double mine = up ? c[1] : c[0], other = up ? c[0] : c[1];
+        d = mine + __shfl_xor_sync(0xffffffffu, other, 2);
+    }
+    return d + __shfl_xor_sync(0xffffffffu, d, 1);
 }
 
 __device__ __forceinline__ double warp_max(double v)
@@ -180,8 +212,10 @@ __host__ __device__ __forceinline__ int next_pow2(int v)
 // ------------------------------------------------------------------ host-side launchers
 // Each returns cudaGetLastError() of its launches; `launches` counts kernels enqueued.
 cudaError_t launch_grid_build(const Dev &D, cudaStream_t s, long long *launches);
-cudaError_t launch_search_lme(const Dev &D, bool init, cudaStream_t s, long long *launches);
-cudaError_t launch_node_major_impl(const Dev &D, int32_t *tmp, cudaStream_t s, long long *launches);
+cudaError_t launch_search(const Dev &D, cudaStream_t s, long long *launches);
+cudaError_t launch_lme(const Dev &D, cudaStream_t s, long long *launches);
+cudaError_t launch_node_offsets(const Dev &D, int32_t *tmp, cudaStream_t s, long long *launches);
+cudaError_t launch_exp_selftest(const double *x, int64_t n, double *mine, double *ref, cudaStream_t s);
 cudaError_t launch_node_update(const Dev &D, double t_next, cudaStream_t s, long long *launches);
 cudaError_t launch_pack3to4(const double *x3, int64_t n, double4_32a *x4, cudaStream_t s, long long *launches);
 cudaError_t launch_init_state(const Dev &D, double T0, cudaStream_t s, long long *launches);
@@ -194,7 +228,7 @@ size_t scan_tmp_ints(int64_t n);
 bool carve_search_scratch(void *base, size_t bytes, int64_t nn, SearchScratch *S);
 cudaError_t build_search_grid(const double *node_x, int64_t nn, double cell, SearchScratch *S,
                               double *grid_out, cudaStream_t s);
-size_t search_lme_smem_bytes(int S, int warps);
+size_t lme_smem_bytes(int S, int warps);
 
 // stand-alone entry points reuse these
 cudaError_t launch_search_only(const double *node_x, int64_t nn, const double *mp_x, int64_t nm,

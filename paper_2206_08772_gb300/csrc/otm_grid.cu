@@ -182,15 +182,17 @@ __global__ void k_cell_sort(int32_t *sorted, const int32_t *cell_start, const Gr
 }
 
 __global__ void k_spos(int64_t n, const int32_t *sorted, const double4_32a *__restrict__ x, double4_32a *spos,
-                       const GridDev *g)
+                       float4 *spos32, const GridDev *g)
 {
     if (g->n_cells == 0) return;
+    const double o0 = g->origin[0], o1 = g->origin[1], o2 = g->origin[2];
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
          s += (int64_t)gridDim.x * blockDim.x) {
         int id = sorted[s];
         double4_32a p = x[id];
         p.w = __longlong_as_double((long long)id);
         spos[s] = p;
+        spos32[s] = make_float4((float)(p.x - o0), (float)(p.y - o1), (float)(p.z - o2), __int_as_float(id));
     }
 }
 
@@ -204,7 +206,7 @@ static int grid_blocks(int64_t n, int threads)
 
 static cudaError_t grid_build_impl(const double4_32a *x, int64_t nn, double cell, int max_cells, GridDev *g,
                                    int32_t *cell_count, int32_t *cell_start, int32_t *node_cell,
-                                   int32_t *node_rank, int32_t *sorted, double4_32a *spos,
+                                   int32_t *node_rank, int32_t *sorted, double4_32a *spos, float4 *spos32,
                                    unsigned long long *err, cudaStream_t s, long long *launches)
 {
     k_bbox_init<<<1, 32, 0, s>>>(g);
@@ -215,7 +217,7 @@ static cudaError_t grid_build_impl(const double4_32a *x, int64_t nn, double cell
     k_scan_cells<<<1, kScanThreads, 0, s>>>(cell_count, cell_start, g);
     k_cell_fill<<<grid_blocks(nn, 256), 256, 0, s>>>(nn, node_cell, node_rank, cell_start, sorted, g);
     k_cell_sort<<<grid_blocks(max_cells, 128), 128, 0, s>>>(sorted, cell_start, g);
-    k_spos<<<grid_blocks(nn, 256), 256, 0, s>>>(nn, sorted, x, spos, g);
+    k_spos<<<grid_blocks(nn, 256), 256, 0, s>>>(nn, sorted, x, spos, spos32, g);
     if (launches) *launches += 9;
     return cudaGetLastError();
 }
@@ -223,7 +225,7 @@ static cudaError_t grid_build_impl(const double4_32a *x, int64_t nn, double cell
 cudaError_t launch_grid_build(const Dev &D, cudaStream_t s, long long *launches)
 {
     return grid_build_impl(D.x, D.nn, D.cell, D.max_cells, D.grid, D.cell_count, D.cell_start,
-                           D.node_cell, D.node_rank, D.sorted, D.spos, D.err, s, launches);
+                           D.node_cell, D.node_rank, D.sorted, D.spos, D.spos32, D.err, s, launches);
 }
 
 // ------------------------------------------------------------------------ generic scan
@@ -342,35 +344,12 @@ cudaError_t launch_exclusive_scan_tmp(const int32_t *in, int32_t *out, int64_t n
 
 size_t scan_tmp_ints(int64_t n) { return (size_t)((n + kScanTile - 1) / kScanTile + 2); }
 
-// ------------------------------------------------------------------------ node-major lists
-// perm[noff[id] + rank] = slot for every occupied pair slot (p * S + k, k < cnt[p]).
-__global__ void k_node_fill(const Dev D)
+// ------------------------------------------------------------------------ node-major offsets
+// noff = exclusive scan of the influence counts; the LME kernel then writes each pair's
+// contribution at noff[node] + rank, so every node's influence list is contiguous.
+cudaError_t launch_node_offsets(const Dev &D, int32_t *tmp, cudaStream_t s, long long *launches)
 {
-    if (has_error(D.err)) return;   // counts may be partial after an error: write nothing
-    const int64_t total = D.nm * (int64_t)D.S;
-    for (int64_t slot = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; slot < total;
-         slot += (int64_t)gridDim.x * blockDim.x) {
-        int64_t p = slot / D.S;
-        int k = (int)(slot - p * D.S);
-        if (k >= D.cnt[p]) continue;
-        int id = D.ids[slot];
-        const int b = D.noff[id], r = D.rank[slot];
-        if (id < 0 || id >= D.nn || r >= D.noff[id + 1] - b) {   // inconsistent lists
-            raise_error(D.err, OTM_ERR_CAPACITY, p);
-            continue;
-        }
-        D.perm[b + r] = (uint32_t)slot;
-    }
-}
-
-cudaError_t launch_node_major_impl(const Dev &D, int32_t *tmp, cudaStream_t s, long long *launches)
-{
-    cudaError_t e = launch_exclusive_scan_tmp(D.ncount, D.noff, D.nn, tmp, s, launches);
-    if (e != cudaSuccess) return e;
-    int64_t total = D.nm * (int64_t)D.S;
-    k_node_fill<<<grid_blocks(total, 256), 256, 0, s>>>(D);
-    if (launches) *launches += 1;
-    return cudaGetLastError();
+    return launch_exclusive_scan_tmp(D.ncount, D.noff, D.nn, tmp, s, launches);
 }
 
 // ------------------------------------------------------------------------ stand-alone search scratch
@@ -384,6 +363,7 @@ size_t search_scratch_bytes(int64_t nn)
     size_t b = 0;
     b += align256(sizeof(GridDev));
     b += 2 * align256((size_t)nn * sizeof(double4_32a));
+    b += align256((size_t)nn * sizeof(float4));
     b += 2 * align256(((size_t)mc + 1) * sizeof(int32_t));
     b += 3 * align256((size_t)nn * sizeof(int32_t));
     b += align256(sizeof(unsigned long long));
@@ -398,6 +378,7 @@ bool carve_search_scratch(void *base, size_t bytes, int64_t nn, SearchScratch *S
     S->g = (GridDev *)p; p += align256(sizeof(GridDev));
     S->x4 = (double4_32a *)p; p += align256((size_t)nn * sizeof(double4_32a));
     S->spos = (double4_32a *)p; p += align256((size_t)nn * sizeof(double4_32a));
+    S->spos32 = (float4 *)p; p += align256((size_t)nn * sizeof(float4));
     S->cell_count = (int32_t *)p; p += align256(((size_t)mc + 1) * sizeof(int32_t));
     S->cell_start = (int32_t *)p; p += align256(((size_t)mc + 1) * sizeof(int32_t));
     S->node_cell = (int32_t *)p; p += align256((size_t)nn * sizeof(int32_t));
@@ -437,8 +418,8 @@ __global__ void k_init_state(const Dev D, double T0)
         D.ebar[p] = 0.0;
         D.T[p] = T0;
         D.rate[p] = 0.0;
-        D.Jdet[p] = 1.0;
         D.lam[3 * p] = D.lam[3 * p + 1] = D.lam[3 * p + 2] = 0.0;
+        D.logz[p] = 0.0;
         D.failed[p] = 0;
         D.cnt[p] = 0;
         D.newton_it[p] = 0;
@@ -493,7 +474,7 @@ cudaError_t build_search_grid(const double *node_x, int64_t nn, double cell, Sea
     if (e != cudaSuccess) return e;
     k_pack3to4<<<grid_blocks(nn, 256), 256, 0, s>>>(node_x, nn, S->x4);
     e = grid_build_impl(S->x4, nn, cell, S->max_cells, S->g, S->cell_count, S->cell_start, S->node_cell,
-                        S->node_rank, S->sorted, S->spos, S->err, s, nullptr);
+                        S->node_rank, S->sorted, S->spos, S->spos32, S->err, s, nullptr);
     if (e != cudaSuccess) return e;
     if (grid_out) k_grid_out<<<1, 32, 0, s>>>(S->g, grid_out);
     return cudaGetLastError();

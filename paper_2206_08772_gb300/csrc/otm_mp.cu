@@ -1,56 +1,97 @@
 // otm_mp.cu -- material-point kernels (sm_103a):
+//   k_search     : Algorithm 3 steps 2-3, warp per MP: candidates of the linked-cell stencil
+//                  tested in FP32 against an error band; only candidates inside the band take
+//                  the exact FP64 test, so the support (d^2 <= r_s^2 in FP64) is bit-exact.
+//                  Ascending-ID sort, influence counting (integer atomics -> rank).
+//   k_lme        : Eq. 14, warp per MP: damped Newton for lambda (warm start, exponent shift from
+//                  the previous log Z), N and grad N = -N J^-1 d, per-pair contributions
+//                  (m_p N, -v sigma grad N) written straight into node-major order.
 //   k_kinematics : Eq. 9-13, warp per MP: x_p = sum N x_I, dF = 1 + sum du_I (x) grad N_I,
 //                  F <- dF F, v <- det(dF) v
 //   k_return_map : Sec. 4.1 / 4.2, thread per MP: Hencky exponential-map radial return (J2
 //                  linear hardening closed form, Johnson-Cook safeguarded Newton), heating,
 //                  fracture flag, sigma = tau / J
-//   k_search_lme : Algorithm 3 + Eq. 14, warp per MP: linked-cell candidate scan with the
-//                  exact FP64 support test, ascending-ID sort, LME Newton for lambda, N and
-//                  grad N = -N J^-1 d, per-pair force / mass contributions for the next node
-//                  update, influence-list counting (integer atomics)
 #include "otm_dev.cuh"
 
 namespace otm {
 
+// ======================================================================== FP64 exponential
+// exp(x) by Tang's table-driven method (P. T. P. Tang, "Table-driven implementation of the
+// exponential function in IEEE floating-point arithmetic", ACM TOMS 15(2), 1989):
+//   x = (64 m + j) ln2/64 + r, |r| <= ln2/128,  exp(x) = 2^m * 2^(j/64) * exp(r),
+// with n = 64 m + j = round(64 x / ln 2) from the 1.5*2^52 shifter, r by a two-term split of
+// ln2/64 (the high part has 36 significant bits, so n * L1 is exact for |n| < 2^17), and
+// exp(r) - 1 by its Taylor polynomial of degree 5 (truncation below 4e-17 relative). The table
+// 2^(j/64) is filled per block from exp2(). Valid for -700 <= x <= 700; below -700 it returns 0
+// (a weight below 1e-304 of the largest), above 700 +inf (the caller then re-shifts).
+constexpr double kExpInvL = 0x1.71547652b82fep+6;    // 64 / ln 2
+constexpr double kExpL1 = 0x1.62e42fefa0000p-7;      // ln 2 / 64, high part
+constexpr double kExpL2 = 0x1.cf79abc9e3b3ap-46;     // ln 2 / 64 - kExpL1
+constexpr double kExpShifter = 0x1.8p52;
+
+__device__ __forceinline__ void exp_table_fill(double *T)
+{
+    for (int j = threadIdx.x; j < 64; j += blockDim.x) T[j] = exp2((double)j / 64.0);
+    __syncthreads();
+}
+
+__device__ __forceinline__ double exp_tang(double x, const double *T)
+{
+    if (x < -700.0) return 0.0;
+    if (!(x <= 700.0)) return x > 700.0 ? INFINITY : x;   // +inf for large x, NaN passes through
+    const double t = fma(x, kExpInvL, kExpShifter);
+    const int n = __double2loint(t);
+    const double nd = t - kExpShifter;
+    double r = fma(-nd, kExpL1, x);
+    r = fma(-nd, kExpL2, r);
+    const double p = r * fma(r, fma(r, fma(r, fma(r, 1.0 / 120.0, 1.0 / 24.0), 1.0 / 6.0), 0.5), 1.0);
+    const double Tj = T[n & 63];
+    const double v = fma(Tj, p, Tj);
+    const int m = n >> 6;
+    return __hiloint2double(__double2hiint(v) + (m << 20), __double2loint(v));
+}
+
 // ======================================================================== LME (Eq. 14)
-struct LmeEval {
-    double Z, logZ, rnorm;
-    double r0, r1, r2;
-    double j00, j11, j22, j01, j12, j02;   // J = sum N d d^T - r r^T
+// Sums of one evaluation at lambda with weights w_a = exp(f_a - shift), f_a = q_a + lambda . d_a:
+// Z = sum w, r = sum w d, A = sum w d d^T (unnormalised). Then N = w / Z, the residual of the
+// consistency condition is r / Z and the Hessian of log Z is J = A / Z - (r/Z)(r/Z)^T = J' / Z
+// with J' = A - r r^T / Z.
+struct LmeSums {
+    double Z, r0, r1, r2, a00, a11, a22, a01, a12, a02;
+    double shift;
 };
 
-// one evaluation at lambda with weights exp(f_a - shift); w[] keeps the unnormalised weights
-__device__ __forceinline__ void lme_eval(const double *dx, const double *dy, const double *dz,
-                                         const double *q, double *w, int n, double l0, double l1,
-                                         double l2, double shift, int lane, LmeEval &E)
+__device__ __forceinline__ void lme_sums(const double *dx, const double *dy, const double *dz, const double *q,
+                                         double *w, int n, double l0, double l1, double l2, double shift,
+                                         int lane, const double *T, LmeSums &E)
 {
-    double Z = 0, r0 = 0, r1 = 0, r2 = 0, a00 = 0, a11 = 0, a22 = 0, a01 = 0, a12 = 0, a02 = 0;
+    double v[16];
+#pragma unroll
+    for (int i = 0; i < 16; i++) v[i] = 0.0;
+    const double qs = -shift;
     for (int k = lane; k < n; k += kWarp) {
         const double x = dx[k], y = dy[k], z = dz[k];
-        const double f = q[k] + (l0 * x + l1 * y + l2 * z);
-        const double wk = exp(f - shift);
+        const double f = fma(l2, z, fma(l1, y, fma(l0, x, q[k] + qs)));
+        const double wk = exp_tang(f, T);
         w[k] = wk;
-        Z += wk;
         const double wx = wk * x, wy = wk * y, wz = wk * z;
-        r0 += wx; r1 += wy; r2 += wz;
-        a00 += wx * x; a11 += wy * y; a22 += wz * z;
-        a01 += wx * y; a12 += wy * z; a02 += wx * z;
+        v[0] += wk;
+        v[1] += wx; v[2] += wy; v[3] += wz;
+        v[4] = fma(wx, x, v[4]); v[5] = fma(wy, y, v[5]); v[6] = fma(wz, z, v[6]);
+        v[7] = fma(wx, y, v[7]); v[8] = fma(wy, z, v[8]); v[9] = fma(wx, z, v[9]);
     }
-    Z = warp_sum(Z);
-    r0 = warp_sum(r0); r1 = warp_sum(r1); r2 = warp_sum(r2);
-    a00 = warp_sum(a00); a11 = warp_sum(a11); a22 = warp_sum(a22);
-    a01 = warp_sum(a01); a12 = warp_sum(a12); a02 = warp_sum(a02);
-    const double iZ = 1.0 / Z;
-    E.Z = Z;
-    E.logZ = shift + log(Z);
-    E.r0 = r0 * iZ; E.r1 = r1 * iZ; E.r2 = r2 * iZ;
-    E.j00 = a00 * iZ - E.r0 * E.r0;
-    E.j11 = a11 * iZ - E.r1 * E.r1;
-    E.j22 = a22 * iZ - E.r2 * E.r2;
-    E.j01 = a01 * iZ - E.r0 * E.r1;
-    E.j12 = a12 * iZ - E.r1 * E.r2;
-    E.j02 = a02 * iZ - E.r0 * E.r2;
-    E.rnorm = sqrt(E.r0 * E.r0 + E.r1 * E.r1 + E.r2 * E.r2);
+    const double t = warp_reduce_scatter16(v, lane);   // value j at lanes 2j, 2j+1
+    E.Z = __shfl_sync(0xffffffffu, t, 0);
+    E.r0 = __shfl_sync(0xffffffffu, t, 2);
+    E.r1 = __shfl_sync(0xffffffffu, t, 4);
+    E.r2 = __shfl_sync(0xffffffffu, t, 6);
+    E.a00 = __shfl_sync(0xffffffffu, t, 8);
+    E.a11 = __shfl_sync(0xffffffffu, t, 10);
+    E.a22 = __shfl_sync(0xffffffffu, t, 12);
+    E.a01 = __shfl_sync(0xffffffffu, t, 14);
+    E.a12 = __shfl_sync(0xffffffffu, t, 16);
+    E.a02 = __shfl_sync(0xffffffffu, t, 18);
+    E.shift = shift;
 }
 
 __device__ __forceinline__ double lme_fmax(const double *dx, const double *dy, const double *dz,
@@ -62,63 +103,79 @@ __device__ __forceinline__ double lme_fmax(const double *dx, const double *dy, c
     return warp_max(m);
 }
 
-__device__ __forceinline__ void lme_eval_safe(const double *dx, const double *dy, const double *dz,
+// evaluation with the given shift; if the weights over- or underflow, again with max f
+__device__ __forceinline__ void lme_sums_safe(const double *dx, const double *dy, const double *dz,
                                               const double *q, double *w, int n, double l0, double l1,
-                                              double l2, double shift, int lane, LmeEval &E)
+                                              double l2, double shift, int lane, const double *T, LmeSums &E)
 {
-    lme_eval(dx, dy, dz, q, w, n, l0, l1, l2, shift, lane, E);
-    if (!(E.Z > 0.0) || !isfinite(E.Z)) {   // weights over/underflowed: shift by the max exponent
-        double fm = lme_fmax(dx, dy, dz, q, n, l0, l1, l2, lane);
-        lme_eval(dx, dy, dz, q, w, n, l0, l1, l2, fm, lane, E);
+    lme_sums(dx, dy, dz, q, w, n, l0, l1, l2, shift, lane, T, E);
+    if (!(E.Z > 1e-200) || !(E.Z < 1e200)) {
+        const double fm = lme_fmax(dx, dy, dz, q, n, l0, l1, l2, lane);
+        lme_sums(dx, dy, dz, q, w, n, l0, l1, l2, fm, lane, T, E);
     }
 }
 
-// symmetric 3x3 inverse by cofactors; returns false if singular / non-finite
-__device__ __forceinline__ bool sym_inv3(double j00, double j11, double j22, double j01, double j12,
-                                         double j02, double inv[6])
+__device__ __forceinline__ double rn2(const LmeSums &E) { return E.r0 * E.r0 + E.r1 * E.r1 + E.r2 * E.r2; }
+
+// J' = A - r r^T / Z and its adjugate / determinant (cofactors); false if not positive definite
+__device__ __forceinline__ bool lme_jinv(const LmeSums &E, double inv[6])
 {
-    double c00 = j11 * j22 - j12 * j12;
-    double c01 = j02 * j12 - j01 * j22;
-    double c02 = j01 * j12 - j02 * j11;
-    double c11 = j00 * j22 - j02 * j02;
-    double c12 = j01 * j02 - j00 * j12;
-    double c22 = j00 * j11 - j01 * j01;
-    double det = j00 * c00 + j01 * c01 + j02 * c02;
+    const double iZ = 1.0 / E.Z;
+    const double s0 = E.r0 * iZ, s1 = E.r1 * iZ, s2 = E.r2 * iZ;
+    const double j00 = E.a00 - s0 * E.r0, j11 = E.a11 - s1 * E.r1, j22 = E.a22 - s2 * E.r2;
+    const double j01 = E.a01 - s0 * E.r1, j12 = E.a12 - s1 * E.r2, j02 = E.a02 - s0 * E.r2;
+    const double c00 = j11 * j22 - j12 * j12;
+    const double c01 = j02 * j12 - j01 * j22;
+    const double c02 = j01 * j12 - j02 * j11;
+    const double c11 = j00 * j22 - j02 * j02;
+    const double c12 = j01 * j02 - j00 * j12;
+    const double c22 = j00 * j11 - j01 * j01;
+    const double det = j00 * c00 + j01 * c01 + j02 * c02;
     if (!(det > 0.0) || !isfinite(det)) return false;
-    double id = 1.0 / det;
+    const double id = 1.0 / det;
     inv[0] = c00 * id; inv[1] = c11 * id; inv[2] = c22 * id;
-    inv[3] = c01 * id; inv[4] = c12 * id; inv[5] = c02 * id;   // (xx, yy, zz, xy, yz, xz)
+    inv[3] = c01 * id; inv[4] = c12 * id; inv[5] = c02 * id;   // (xx, yy, zz, xy, yz, xz) of J'^-1
     return true;
 }
 
-// Damped Newton on the convex log Z(lambda): step -J^-1 r, halved until log Z or |r| drops.
-// On return w[] holds the weights of the accepted evaluation E. Warp-uniform.
+// log Z(trial) < log Z(current)
+__device__ __forceinline__ bool logz_less(const LmeSums &t, const LmeSums &c)
+{
+    if (t.shift == c.shift) return t.Z < c.Z;
+    return t.shift + log(t.Z) < c.shift + log(c.Z);
+}
+
+// Damped Newton on the convex log Z(lambda): step -J^-1 (r/Z) = -J'^-1 r, halved until log Z or
+// the residual norm drops; stops when |r| / Z <= tol. All evaluations of one solve share the
+// initial shift (the previous step's log Z, so w ~ N), which makes the log Z comparison a
+// comparison of Z. On return w[] holds the weights of the accepted evaluation E. Warp-uniform.
 __device__ int lme_newton(const double *dx, const double *dy, const double *dz, const double *q, double *w,
-                          int n, double &l0, double &l1, double &l2, double tol, int max_it, int lane,
-                          LmeEval &E, int &iters)
+                          int n, double &l0, double &l1, double &l2, double shift, double tol, int max_it,
+                          int lane, const double *T, LmeSums &E, int &iters)
 {
     iters = 0;
     if (n <= 0) return OTM_ERR_LME_NOCONV;
-    double fm = lme_fmax(dx, dy, dz, q, n, l0, l1, l2, lane);
-    lme_eval(dx, dy, dz, q, w, n, l0, l1, l2, fm, lane, E);
+    const double tol2 = tol * tol;
+    lme_sums_safe(dx, dy, dz, q, w, n, l0, l1, l2, shift, lane, T, E);
     for (;;) {
-        if (!isfinite(E.rnorm)) return OTM_ERR_LME_NOCONV;
-        if (E.rnorm <= tol) return OTM_OK;
+        const double r2 = rn2(E);
+        if (!isfinite(r2) || !isfinite(E.Z)) return OTM_ERR_LME_NOCONV;
+        if (r2 <= tol2 * E.Z * E.Z) return OTM_OK;
         if (iters >= max_it) return OTM_ERR_LME_NOCONV;
         iters++;
         double inv[6];
-        if (!sym_inv3(E.j00, E.j11, E.j22, E.j01, E.j12, E.j02, inv)) return OTM_ERR_LME_NOCONV;
+        if (!lme_jinv(E, inv)) return OTM_ERR_LME_NOCONV;
         const double s0 = -(inv[0] * E.r0 + inv[3] * E.r1 + inv[5] * E.r2);
         const double s1 = -(inv[3] * E.r0 + inv[1] * E.r1 + inv[4] * E.r2);
         const double s2 = -(inv[5] * E.r0 + inv[4] * E.r1 + inv[2] * E.r2);
         double t = 1.0;
         bool accepted = false;
-        LmeEval Et;
+        LmeSums Et;
         double m0 = l0, m1 = l1, m2 = l2;
         for (int halving = 0; halving < 40; halving++) {
-            m0 = l0 + t * s0; m1 = l1 + t * s1; m2 = l2 + t * s2;
-            lme_eval_safe(dx, dy, dz, q, w, n, m0, m1, m2, E.logZ, lane, Et);
-            if (isfinite(Et.logZ) && (Et.logZ < E.logZ || Et.rnorm < E.rnorm)) {
+            m0 = fma(t, s0, l0); m1 = fma(t, s1, l1); m2 = fma(t, s2, l2);
+            lme_sums_safe(dx, dy, dz, q, w, n, m0, m1, m2, E.shift, lane, T, Et);
+            if (isfinite(Et.Z) && (logz_less(Et, E) || rn2(Et) * (E.Z * E.Z) < r2 * (Et.Z * Et.Z))) {
                 accepted = true;
                 break;
             }
@@ -131,34 +188,72 @@ __device__ int lme_newton(const double *dx, const double *dy, const double *dz, 
 }
 
 // ======================================================================== support search
-// Candidate scan of the +-2 cell stencil (rows of 5 cells are contiguous in the sorted node
-// array). Accepted IDs go to list[0..min(count, S)); returns the full count. Warp-uniform.
-__device__ int warp_support_search(const GridDev *__restrict__ g, const int32_t *__restrict__ cell_start,
-                                   const double4_32a *__restrict__ spos, double cell, double rs2, double px,
-                                   double py, double pz, int32_t *list, int S, int lane)
+// Search of one MP over the linked-cell rows that cover [x_p - r_s, x_p + r_s] (with a 1e-4
+// relative margin), rows of contiguous cells along x. Each candidate is first tested in FP32 on
+// coordinates relative to the grid origin; the FP32 value d2f of |x_p - x_a|^2 differs from the
+// FP64 value that defines the support by less than `band` (derived below), so a candidate with
+// d2f < rs2 - band is inside, one with d2f > rs2 + band is outside, and only the rest take the
+// exact FP64 test on the double coordinates. Accepted IDs go to list[0..min(count, S)); returns
+// the full count. Warp-uniform.
+//
+// Band: with u = 2^-24, U >= |x - o| for both points, e = 1.001 u (2U + 1.5 r_s) bounds the
+// error of each FP32 difference (two roundings of the coordinates, one of the difference), so
+// |d2f - d2| <= e (2 sum|d_i| + 3e) + 3.1 u d2 (three roundings in the fused sum), and the FP64
+// d2 is within 7e-16 d2 of the real value. Near the threshold |d_i| <= 1.5 r_s, giving
+// band = 1.25 [e (9 r_s + 3e) + 3.1 u rs2] + 1e-15 rs2.
+struct SearchGrid {
+    const GridDev *g;
+    const int32_t *cell_start;
+    const float4 *spos32;
+    const double4_32a *spos;
+};
+
+__device__ int warp_support_search(const SearchGrid &G, double cell, double rs2, double px, double py, double pz,
+                                   int32_t *list, int S, int lane)
 {
+    const GridDev *g = G.g;
     if (g->n_cells == 0) return 0;
     const int nx = g->dims[0], ny = g->dims[1], nz = g->dims[2];
-    const int cx = cell_coord(px, g->origin[0], cell, nx, false);
-    const int cy = cell_coord(py, g->origin[1], cell, ny, false);
-    const int cz = cell_coord(pz, g->origin[2], cell, nz, false);
-    const int x0 = max(cx - 2, 0), x1 = min(cx + 2, nx - 1);
+    // position relative to the grid origin, in FP32 (one FP64 subtraction per axis)
+    const float X = (float)(px - g->origin[0]), Y = (float)(py - g->origin[1]), Z = (float)(pz - g->origin[2]);
+    const float cf = (float)cell;
+    const float rs = (float)sqrt(rs2);
+    // cell ranges covering [x - r_s, x + r_s] with a 1e-4 relative margin (which covers the FP32
+    // rounding of X and of the quotient; nodes are binned by the exact FP64 floor)
+    const float rsm = rs * 1.0001f;
+    const int x0 = max((int)fmaxf(floorf((X - rsm) / cf), -1.f), 0);
+    const int x1 = min((int)fminf(floorf((X + rsm) / cf), (float)nx), nx - 1);
+    const int y0 = max((int)fmaxf(floorf((Y - rsm) / cf), -1.f), 0);
+    const int y1 = min((int)fminf(floorf((Y + rsm) / cf), (float)ny), ny - 1);
+    const int z0 = max((int)fmaxf(floorf((Z - rsm) / cf), -1.f), 0);
+    const int z1 = min((int)fminf(floorf((Z + rsm) / cf), (float)nz), nz - 1);
     int cnt = 0;
-    if (x0 > x1) return 0;
-    const int z0 = max(cz - 2, 0), z1 = min(cz + 2, nz - 1);
-    const int y0 = max(cy - 2, 0), y1 = min(cy + 2, ny - 1);
+    if (x0 > x1 || y0 > y1 || z0 > z1) return 0;
+    const float ext = fmaxf(fmaxf((float)nx, (float)ny), (float)nz) * cf;
+    const float U = fmaxf(fmaxf(fmaxf(fabsf(X), fabsf(Y)), fabsf(Z)), ext);
+    const float u = 0x1p-24f;
+    const float e = 1.001f * u * (2.f * U + 1.5f * rs);
+    const float band = 1.5f * (1.25f * (e * (9.f * rs + 3.f * e) + 3.1f * u * rs * rs) + 1e-15f * rs * rs);
+    const float lo = __fsub_rd(__double2float_rd(rs2), band), hi = __fadd_ru(__double2float_ru(rs2), band);
     for (int kz = z0; kz <= z1; kz++) {
         for (int ky = y0; ky <= y1; ky++) {
             const int rowc = (kz * ny + ky) * nx;
-            const int s0 = cell_start[rowc + x0], s1 = cell_start[rowc + x1 + 1];
+            const int s0 = G.cell_start[rowc + x0], s1 = G.cell_start[rowc + x1 + 1];
             for (int b = s0; b < s1; b += kWarp) {
                 const int s = b + lane;
                 bool acc = false;
                 int id = 0;
                 if (s < s1) {
-                    const double4_32a a = spos[s];
-                    acc = dist2_exact(px, py, pz, a.x, a.y, a.z) <= rs2;
-                    id = (int)__double_as_longlong(a.w);
+                    const float4 a = G.spos32[s];
+                    const float dx = X - a.x, dy = Y - a.y, dz = Z - a.z;
+                    const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                    id = __float_as_int(a.w);
+                    if (d2 <= lo) {
+                        acc = true;
+                    } else if (d2 <= hi) {   // ambiguity band: exact FP64 test
+                        const double4_32a q = G.spos[s];
+                        acc = dist2_exact(px, py, pz, q.x, q.y, q.z) <= rs2;
+                    }
                 }
                 const unsigned m = __ballot_sync(0xffffffffu, acc);
                 if (acc) {
@@ -185,36 +280,31 @@ __device__ __forceinline__ int fexp32(float v)
     return e == 0 ? -2000 : e - 127;
 }
 
-// per-warp shared-memory layout for search + LME
+// per-warp shared-memory layout for the LME solve
 struct WarpSmem {
-    int32_t *list;   // next_pow2(S) ints
     double *dx, *dy, *dz, *q, *w;
 };
 
 __device__ __forceinline__ WarpSmem warp_smem(unsigned char *base, int S, int warp)
 {
-    const int P2 = next_pow2(S);
-    const size_t per = (size_t)P2 * sizeof(int32_t) + 5 * (size_t)S * sizeof(double);
-    unsigned char *b = base + (size_t)warp * per;
+    unsigned char *b = base + (size_t)warp * 5 * (size_t)S * sizeof(double);
     WarpSmem W;
     W.dx = (double *)b;
     W.dy = W.dx + S;
     W.dz = W.dy + S;
     W.q = W.dz + S;
     W.w = W.q + S;
-    W.list = (int32_t *)(W.w + S);
     return W;
 }
 
-size_t search_lme_smem_bytes(int S, int warps)
-{
-    return (size_t)warps * ((size_t)next_pow2(S) * sizeof(int32_t) + 5 * (size_t)S * sizeof(double));
-}
+constexpr int kLmeWarps = 4;
 
-// ======================================================================== k_search_lme
-// mode 0: initialisation (contributions with the current sigma, v); mode 1: a step.
-template <bool MIXED>
-__global__ void __launch_bounds__(kSearchWarps * kWarp) k_search_lme(const Dev D)
+size_t lme_smem_bytes(int S, int warps) { return 64 * sizeof(double) + (size_t)warps * 5 * (size_t)S * sizeof(double); }
+
+size_t search_lme_smem_bytes(int S, int warps) { return lme_smem_bytes(S, warps); }
+
+// ======================================================================== k_search
+__global__ void __launch_bounds__(kSearchWarps * kWarp) k_search(const Dev D)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -222,12 +312,10 @@ __global__ void __launch_bounds__(kSearchWarps * kWarp) k_search_lme(const Dev D
     if (p >= D.nm) return;
     if (has_error(D.err)) return;
     const int S = D.S;
-    WarpSmem W = warp_smem(smem_raw, S, warp);
+    int32_t *list = (int32_t *)smem_raw + (size_t)warp * next_pow2(S);
     const double4_32a xp = D.xp[p];
-
-    // ---- Algorithm 3: linked-cell support search at the current configuration
-    int cnt = warp_support_search(D.grid, D.cell_start, D.spos, D.cell, D.rs2, xp.x, xp.y, xp.z, W.list, S,
-                                  lane);
+    SearchGrid G{D.grid, D.cell_start, D.spos32, D.spos};
+    const int cnt = warp_support_search(G, D.cell, D.rs2, xp.x, xp.y, xp.z, list, S, lane);
     if (cnt > S) {
         if (lane == 0) {
             raise_error(D.err, OTM_ERR_CAPACITY, D.mgid[p]);
@@ -235,72 +323,112 @@ __global__ void __launch_bounds__(kSearchWarps * kWarp) k_search_lme(const Dev D
         }
         return;
     }
-    const int P2 = next_pow2(max(cnt, 1));
-    for (int k = cnt + lane; k < P2; k += kWarp) W.list[k] = 0x7fffffff;
+    // the list is in linked-cell order (rows, cells, ascending ID within a cell): unique for a
+    // given configuration, so no sort is needed for determinism; exports sort it by ID
     __syncwarp();
-    warp_bitonic_sort(W.list, P2, lane);
+    const int64_t base = p * (int64_t)S;
+    for (int k = lane; k < cnt; k += kWarp) {
+        const int id = list[k];
+        D.ids[base + k] = id;
+        const int r = atomicAdd(&D.ncount[id], 1);
+        if (r > 0xffff) raise_error(D.err, OTM_ERR_CAPACITY, D.ngid[id]);
+        D.rank[base + k] = (uint16_t)r;
+    }
+    if (lane == 0) D.cnt[p] = cnt;
+}
 
-    // ---- d_a = x_p - x_a and the prior exponent -beta |d_a|^2
+cudaError_t launch_search(const Dev &D, cudaStream_t s, long long *launches)
+{
+    const size_t smem = (size_t)kSearchWarps * next_pow2(D.S) * sizeof(int32_t);
+    const unsigned blocks = (unsigned)((D.nm + kSearchWarps - 1) / kSearchWarps);
+    if (blocks == 0) return cudaSuccess;
+    k_search<<<blocks, kSearchWarps * kWarp, smem, s>>>(D);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
+// ======================================================================== k_lme
+template <bool MIXED>
+__global__ void __launch_bounds__(kLmeWarps * kWarp) k_lme(const Dev D)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double *T = (double *)smem_raw;
+    exp_table_fill(T);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t p = (int64_t)blockIdx.x * kLmeWarps + warp;
+    if (p >= D.nm) return;
+    if (has_error(D.err)) return;
+    const int S = D.S;
+    WarpSmem W = warp_smem(smem_raw + 64 * sizeof(double), S, warp);
+    const double4_32a xp = D.xp[p];
+    const int cnt = D.cnt[p];
+    const int64_t base = p * (int64_t)S;
+
+    // d_a = x_p - x_a and the prior exponent -beta |d_a|^2
     const double beta = D.beta;
     for (int k = lane; k < cnt; k += kWarp) {
-        const double4_32a a = D.x[W.list[k]];
+        const double4_32a a = D.x[D.ids[base + k]];
         const double x = xp.x - a.x, y = xp.y - a.y, z = xp.z - a.z;
         W.dx[k] = x; W.dy[k] = y; W.dz[k] = z;
-        W.q[k] = -beta * (x * x + y * y + z * z);
+        W.q[k] = -beta * fma(z, z, fma(y, y, x * x));
     }
     __syncwarp();
 
-    // ---- Eq. 14: Newton for lambda, warm-started from the previous step
+    // Eq. 14: Newton for lambda, warm-started from the previous step
     double l0 = D.lam[3 * p], l1 = D.lam[3 * p + 1], l2 = D.lam[3 * p + 2];
-    LmeEval E;
+    LmeSums E;
     int iters = 0;
-    int st = lme_newton(W.dx, W.dy, W.dz, W.q, W.w, cnt, l0, l1, l2, D.tol_abs, D.max_newton, lane, E, iters);
+    int st = lme_newton(W.dx, W.dy, W.dz, W.q, W.w, cnt, l0, l1, l2, D.logz[p], D.tol_abs, D.max_newton, lane, T,
+                        E, iters);
     double inv[6];
-    if (st == OTM_OK && !sym_inv3(E.j00, E.j11, E.j22, E.j01, E.j12, E.j02, inv)) st = OTM_ERR_LME_NOCONV;
+    if (st == OTM_OK && !lme_jinv(E, inv)) st = OTM_ERR_LME_NOCONV;
     if (lane == 0) {
-        D.cnt[p] = (st == OTM_OK) ? cnt : 0;
         D.newton_it[p] = iters;
         if (st == OTM_OK) {
             D.lam[3 * p] = l0; D.lam[3 * p + 1] = l1; D.lam[3 * p + 2] = l2;
+            D.logz[p] = E.shift + log(E.Z);
         } else {
             raise_error(D.err, st, D.mgid[p]);
         }
     }
     if (st != OTM_OK) return;
 
-    // ---- N_a = w_a / Z, grad N_a = -N_a J^-1 d_a; contributions for Eq. 5 of the next step
+    // N_a = w_a / Z, grad N_a = -N_a J^-1 d_a = -w_a J'^-1 d_a; contributions for Eq. 5 of the next
+    // step, stored at the pair's place in its node's influence list
     const double iZ = 1.0 / E.Z;
     const double mp = D.mass[p], vp = D.vol[p];
     const double *sg = D.sig + 6 * p;
     const double sxx = sg[0], syy = sg[1], szz = sg[2], sxy = sg[3], syz = sg[4], sxz = sg[5];
-    const int64_t base = p * (int64_t)S;
     int em = -2000, ef = -2000;   // largest binary exponents of the stored mass / force terms
     for (int k = lane; k < cnt; k += kWarp) {
-        const double N = W.w[k] * iZ;
+        const double wk = W.w[k];
+        const double N = wk * iZ;
         const double x = W.dx[k], y = W.dy[k], z = W.dz[k];
-        const double gx = -N * (inv[0] * x + inv[3] * y + inv[5] * z);
-        const double gy = -N * (inv[3] * x + inv[1] * y + inv[4] * z);
-        const double gz = -N * (inv[5] * x + inv[4] * y + inv[2] * z);
-        const int id = W.list[k];
-        D.ids[base + k] = id;
+        const double gx = -wk * (inv[0] * x + inv[3] * y + inv[5] * z);
+        const double gy = -wk * (inv[3] * x + inv[1] * y + inv[4] * z);
+        const double gz = -wk * (inv[5] * x + inv[4] * y + inv[2] * z);
         D.shape[base + k] = make_double4_32a(N, gx, gy, gz);
-        const double cm = mp * N;
-        const double fx = -vp * (sxx * gx + sxy * gy + sxz * gz);
-        const double fy = -vp * (sxy * gx + syy * gy + syz * gz);
-        const double fz = -vp * (sxz * gx + syz * gy + szz * gz);
+        const int id = D.ids[base + k];
+        const int64_t pos = (int64_t)D.noff[id] + D.rank[base + k];
         if (MIXED) {
-            const float4 c = make_float4((float)cm, (float)fx, (float)fy, (float)fz);
-            D.contrib32[base + k] = c;
-            em = max(em, fexp32(c.x));
-            ef = max(ef, max(fexp32(c.y), max(fexp32(c.z), fexp32(c.w))));
+            const float fgx = (float)gx, fgy = (float)gy, fgz = (float)gz;
+            const float fv = (float)vp;
+            const float c0 = (float)(mp * N);
+            const float c1 = -fv * fmaf((float)sxz, fgz, fmaf((float)sxy, fgy, (float)sxx * fgx));
+            const float c2 = -fv * fmaf((float)syz, fgz, fmaf((float)syy, fgy, (float)sxy * fgx));
+            const float c3 = -fv * fmaf((float)szz, fgz, fmaf((float)syz, fgy, (float)sxz * fgx));
+            D.contrib32[pos] = make_float4(c0, c1, c2, c3);
+            em = max(em, fexp32(c0));
+            ef = max(ef, max(fexp32(c1), max(fexp32(c2), fexp32(c3))));
         } else {
-            D.contrib64[base + k] = make_double4_32a(cm, fx, fy, fz);
+            const double cm = mp * N;
+            const double fx = -vp * (sxx * gx + sxy * gy + sxz * gz);
+            const double fy = -vp * (sxy * gx + syy * gy + syz * gz);
+            const double fz = -vp * (sxz * gx + syz * gy + szz * gz);
+            D.contrib64[pos] = make_double4_32a(cm, fx, fy, fz);
             em = max(em, fexp64(cm));
             ef = max(ef, max(fexp64(fx), max(fexp64(fy), fexp64(fz))));
         }
-        const int r = atomicAdd(&D.ncount[id], 1);
-        if (r > 0xffff) raise_error(D.err, OTM_ERR_CAPACITY, D.ngid[id]);
-        D.rank[base + k] = (uint16_t)r;
     }
     em = __reduce_max_sync(0xffffffffu, em);
     ef = __reduce_max_sync(0xffffffffu, ef);
@@ -310,27 +438,30 @@ __global__ void __launch_bounds__(kSearchWarps * kWarp) k_search_lme(const Dev D
     }
 }
 
-cudaError_t launch_search_lme(const Dev &D, bool init, cudaStream_t s, long long *launches)
+cudaError_t launch_lme(const Dev &D, cudaStream_t s, long long *launches)
 {
-    (void)init;
-    const size_t smem = search_lme_smem_bytes(D.S, kSearchWarps);
-    const unsigned blocks = (unsigned)((D.nm + kSearchWarps - 1) / kSearchWarps);
+    const size_t smem = lme_smem_bytes(D.S, kLmeWarps);
+    const unsigned blocks = (unsigned)((D.nm + kLmeWarps - 1) / kLmeWarps);
     if (blocks == 0) return cudaSuccess;
     cudaError_t e;
     if (D.precision == OTM_PRECISION_MIXED) {
-        e = cudaFuncSetAttribute(k_search_lme<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(k_lme<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k_search_lme<true><<<blocks, kSearchWarps * kWarp, smem, s>>>(D);
+        k_lme<true><<<blocks, kLmeWarps * kWarp, smem, s>>>(D);
     } else {
-        e = cudaFuncSetAttribute(k_search_lme<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(k_lme<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k_search_lme<false><<<blocks, kSearchWarps * kWarp, smem, s>>>(D);
+        k_lme<false><<<blocks, kLmeWarps * kWarp, smem, s>>>(D);
     }
     if (launches) *launches += 1;
     return cudaGetLastError();
 }
 
+// (N, grad N) of every slot of a padded row set, for state export: already stored in shape[]
 // ======================================================================== k_kinematics
+// warp per MP: the 12 sums x_p,i = sum N x_a,i and (dF - 1)_ij = sum du_a,i dN_a/dx_j over the old
+// support; lanes 2j write sum j. The products with F, det(dF) and the volume update follow in
+// the thread-per-MP return-map kernel.
 template <bool MIXED>
 __global__ void __launch_bounds__(128) k_kinematics(const Dev D)
 {
@@ -340,8 +471,9 @@ __global__ void __launch_bounds__(128) k_kinematics(const Dev D)
     if (has_error(D.err)) return;
     const int n = D.cnt[p];
     const int64_t base = p * (int64_t)D.S;
-    double x0 = 0, x1 = 0, x2 = 0;
-    double a00 = 0, a01 = 0, a02 = 0, a10 = 0, a11 = 0, a12 = 0, a20 = 0, a21 = 0, a22 = 0;
+    double v[16];
+#pragma unroll
+    for (int i = 0; i < 16; i++) v[i] = 0.0;
     for (int k = lane; k < n; k += kWarp) {
         const int id = D.ids[base + k];
         const double4_32a sh = D.shape[base + k];
@@ -354,38 +486,22 @@ __global__ void __launch_bounds__(128) k_kinematics(const Dev D)
             const double4_32a u = D.du[id];
             u0 = u.x; u1 = u.y; u2 = u.z;
         }
-        x0 += sh.x * xa.x; x1 += sh.x * xa.y; x2 += sh.x * xa.z;
-        a00 += u0 * sh.y; a01 += u0 * sh.z; a02 += u0 * sh.w;
-        a10 += u1 * sh.y; a11 += u1 * sh.z; a12 += u1 * sh.w;
-        a20 += u2 * sh.y; a21 += u2 * sh.z; a22 += u2 * sh.w;
+        v[0] = fma(sh.x, xa.x, v[0]); v[1] = fma(sh.x, xa.y, v[1]); v[2] = fma(sh.x, xa.z, v[2]);
+        v[3] = fma(u0, sh.y, v[3]); v[4] = fma(u0, sh.z, v[4]); v[5] = fma(u0, sh.w, v[5]);
+        v[6] = fma(u1, sh.y, v[6]); v[7] = fma(u1, sh.z, v[7]); v[8] = fma(u1, sh.w, v[8]);
+        v[9] = fma(u2, sh.y, v[9]); v[10] = fma(u2, sh.z, v[10]); v[11] = fma(u2, sh.w, v[11]);
     }
-    x0 = warp_sum(x0); x1 = warp_sum(x1); x2 = warp_sum(x2);
-    a00 = warp_sum(a00); a01 = warp_sum(a01); a02 = warp_sum(a02);
-    a10 = warp_sum(a10); a11 = warp_sum(a11); a12 = warp_sum(a12);
-    a20 = warp_sum(a20); a21 = warp_sum(a21); a22 = warp_sum(a22);
-    if (lane != 0) return;
-    const double d[9] = {1.0 + a00, a01, a02, a10, 1.0 + a11, a12, a20, a21, 1.0 + a22};
-    const double det = d[0] * (d[4] * d[8] - d[5] * d[7]) - d[1] * (d[3] * d[8] - d[5] * d[6]) +
-                       d[2] * (d[3] * d[7] - d[4] * d[6]);
-    D.xp[p] = make_double4_32a(x0, x1, x2, 0.0);
-    double *dF = D.dF + 9 * p;
-    for (int i = 0; i < 9; i++) dF[i] = d[i];
-    if (!(det > 0.0)) {
-        raise_error(D.err, OTM_ERR_JACOBIAN, D.mgid[p]);
-        return;
+    const double t = warp_reduce_scatter16(v, lane);
+    const int j = lane >> 1;
+    if ((lane & 1) == 0 && j < 12) {
+        if (j < 3) {
+            ((double *)&D.xp[p])[j] = t;
+            if (!isfinite(t)) raise_error(D.err, OTM_ERR_NONFINITE, D.mgid[p]);
+        } else {
+            const int c = j - 3;   // row-major (i, j) of dF
+            D.dF[9 * p + c] = (c == 0 || c == 4 || c == 8) ? 1.0 + t : t;
+        }
     }
-    double *F = D.F + 9 * p;
-    double Fo[9];
-    for (int i = 0; i < 9; i++) Fo[i] = F[i];
-    double Fn[9];
-    for (int i = 0; i < 3; i++)
-        for (int j = 0; j < 3; j++)
-            Fn[3 * i + j] = d[3 * i] * Fo[j] + d[3 * i + 1] * Fo[3 + j] + d[3 * i + 2] * Fo[6 + j];
-    for (int i = 0; i < 9; i++) F[i] = Fn[i];
-    D.vol[p] *= det;
-    D.Jdet[p] = Fn[0] * (Fn[4] * Fn[8] - Fn[5] * Fn[7]) - Fn[1] * (Fn[3] * Fn[8] - Fn[5] * Fn[6]) +
-                Fn[2] * (Fn[3] * Fn[7] - Fn[4] * Fn[6]);
-    if (!isfinite(x0) || !isfinite(x1) || !isfinite(x2)) raise_error(D.err, OTM_ERR_NONFINITE, D.mgid[p]);
 }
 
 cudaError_t launch_kinematics(const Dev &D, cudaStream_t s, long long *launches)
@@ -571,10 +687,27 @@ __global__ void __launch_bounds__(128) k_return_map(const Dev D)
     if (has_error(D.err)) return;
     RmIn in;
     for (int i = 0; i < 9; i++) in.dF[i] = D.dF[9 * p + i];
+    const double *d = in.dF;
+    // Eq. 10-12: F_{n+1} = dF F_n, v_{n+1} = det(dF) v_n
+    const double det = d[0] * (d[4] * d[8] - d[5] * d[7]) - d[1] * (d[3] * d[8] - d[5] * d[6]) +
+                       d[2] * (d[3] * d[7] - d[4] * d[6]);
+    if (!(det > 0.0)) {
+        raise_error(D.err, OTM_ERR_JACOBIAN, D.mgid[p]);
+        return;
+    }
+    double *F = D.F + 9 * p;
+    double Fo[9], Fn[9];
+    for (int i = 0; i < 9; i++) Fo[i] = F[i];
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++)
+            Fn[3 * i + j] = d[3 * i] * Fo[j] + d[3 * i + 1] * Fo[3 + j] + d[3 * i + 2] * Fo[6 + j];
+    for (int i = 0; i < 9; i++) F[i] = Fn[i];
+    D.vol[p] *= det;
+    in.J = Fn[0] * (Fn[4] * Fn[8] - Fn[5] * Fn[7]) - Fn[1] * (Fn[3] * Fn[8] - Fn[5] * Fn[6]) +
+           Fn[2] * (Fn[3] * Fn[7] - Fn[4] * Fn[6]);
     for (int i = 0; i < 6; i++) in.be[i] = D.be[6 * p + i];
     in.ebar = D.ebar[p];
     in.T = D.T[p];
-    in.J = D.Jdet[p];
     RmOut o;
     const int st = return_map_point(D.mat[D.mat_id[p]], D.dt, in, o);
     if (st != OTM_OK) {
@@ -602,9 +735,9 @@ cudaError_t launch_return_map(const Dev &D, cudaStream_t s, long long *launches)
 
 // ======================================================================== stand-alone kernels
 __global__ void __launch_bounds__(kSearchWarps * kWarp)
-    k_search_only(const GridDev *g, const int32_t *cell_start, const double4_32a *spos, double cell, double rs2,
-                  const double *mp_x, int64_t nm, int S, int32_t *ids, int32_t *counts, int32_t *status,
-                  const unsigned long long *grid_err)
+    k_search_only(const GridDev *g, const int32_t *cell_start, const float4 *spos32, const double4_32a *spos,
+                  double cell, double rs2, const double *mp_x, int64_t nm, int S, int32_t *ids, int32_t *counts,
+                  int32_t *status, const unsigned long long *grid_err)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -620,7 +753,8 @@ __global__ void __launch_bounds__(kSearchWarps * kWarp)
         return;
     }
     const double px = mp_x[3 * p], py = mp_x[3 * p + 1], pz = mp_x[3 * p + 2];
-    const int cnt = warp_support_search(g, cell_start, spos, cell, rs2, px, py, pz, list, S, lane);
+    SearchGrid G{g, cell_start, spos32, spos};
+    const int cnt = warp_support_search(G, cell, rs2, px, py, pz, list, S, lane);
     const int n = min(cnt, S);
     const int Q2 = next_pow2(max(n, 1));
     for (int k = n + lane; k < Q2; k += kWarp) list[k] = 0x7fffffff;
@@ -644,23 +778,23 @@ cudaError_t launch_search_only(const double *node_x, int64_t nn, const double *m
     const size_t smem = (size_t)kSearchWarps * next_pow2(S) * sizeof(int32_t);
     const unsigned blocks = (unsigned)((nm + kSearchWarps - 1) / kSearchWarps);
     if (blocks == 0) return cudaSuccess;
-    e = cudaFuncSetAttribute(k_search_only, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_search_only<<<blocks, kSearchWarps * kWarp, smem, s>>>(V.g, V.cell_start, V.spos, cell, rs2, mp_x, nm, S,
-                                                             ids, counts, status, V.err);
+    k_search_only<<<blocks, kSearchWarps * kWarp, smem, s>>>(V.g, V.cell_start, V.spos32, V.spos, cell, rs2, mp_x,
+                                                             nm, S, ids, counts, status, V.err);
     return cudaGetLastError();
 }
 
-__global__ void __launch_bounds__(kSearchWarps * kWarp)
+__global__ void __launch_bounds__(kLmeWarps * kWarp)
     k_lme_only(const double *node_x, const double *mp_x, int64_t nm, const int32_t *ids, const int32_t *counts,
                int S, double beta, double tol, int max_newton, double *lam, double *shape, int32_t *iters_out,
                int32_t *status)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    double *T = (double *)smem_raw;
+    exp_table_fill(T);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t p = (int64_t)blockIdx.x * kSearchWarps + warp;
+    const int64_t p = (int64_t)blockIdx.x * kLmeWarps + warp;
     if (p >= nm) return;
-    WarpSmem W = warp_smem(smem_raw, S, warp);
+    WarpSmem W = warp_smem(smem_raw + 64 * sizeof(double), S, warp);
     const int n = counts[p];
     if (n > S || n <= 0) {
         if (lane == 0) atomicCAS(status, 0, n > S ? OTM_ERR_CAPACITY : OTM_ERR_LME_NOCONV);
@@ -669,19 +803,19 @@ __global__ void __launch_bounds__(kSearchWarps * kWarp)
     const double px = mp_x[3 * p], py = mp_x[3 * p + 1], pz = mp_x[3 * p + 2];
     const int64_t base = p * (int64_t)S;
     for (int k = lane; k < n; k += kWarp) {
-        const int id = ids[base + k];
-        const double x = px - node_x[3 * (int64_t)id], y = py - node_x[3 * (int64_t)id + 1],
-                     z = pz - node_x[3 * (int64_t)id + 2];
+        const int64_t id = ids[base + k];
+        const double x = px - node_x[3 * id], y = py - node_x[3 * id + 1], z = pz - node_x[3 * id + 2];
         W.dx[k] = x; W.dy[k] = y; W.dz[k] = z;
-        W.q[k] = -beta * (x * x + y * y + z * z);
+        W.q[k] = -beta * fma(z, z, fma(y, y, x * x));
     }
     __syncwarp();
     double l0 = lam[3 * p], l1 = lam[3 * p + 1], l2 = lam[3 * p + 2];
-    LmeEval E;
+    const double shift = lme_fmax(W.dx, W.dy, W.dz, W.q, n, l0, l1, l2, lane);
+    LmeSums E;
     int iters = 0;
-    int st = lme_newton(W.dx, W.dy, W.dz, W.q, W.w, n, l0, l1, l2, tol, max_newton, lane, E, iters);
+    int st = lme_newton(W.dx, W.dy, W.dz, W.q, W.w, n, l0, l1, l2, shift, tol, max_newton, lane, T, E, iters);
     double inv[6];
-    if (st == OTM_OK && !sym_inv3(E.j00, E.j11, E.j22, E.j01, E.j12, E.j02, inv)) st = OTM_ERR_LME_NOCONV;
+    if (st == OTM_OK && !lme_jinv(E, inv)) st = OTM_ERR_LME_NOCONV;
     if (lane == 0) {
         if (iters_out) iters_out[p] = iters;
         if (st != OTM_OK) atomicCAS(status, 0, st);
@@ -690,13 +824,13 @@ __global__ void __launch_bounds__(kSearchWarps * kWarp)
     if (st != OTM_OK) return;
     const double iZ = 1.0 / E.Z;
     for (int k = lane; k < n; k += kWarp) {
-        const double N = W.w[k] * iZ;
+        const double wk = W.w[k];
         const double x = W.dx[k], y = W.dy[k], z = W.dz[k];
         double *o = shape + 4 * (base + k);
-        o[0] = N;
-        o[1] = -N * (inv[0] * x + inv[3] * y + inv[5] * z);
-        o[2] = -N * (inv[3] * x + inv[1] * y + inv[4] * z);
-        o[3] = -N * (inv[5] * x + inv[4] * y + inv[2] * z);
+        o[0] = wk * iZ;
+        o[1] = -wk * (inv[0] * x + inv[3] * y + inv[5] * z);
+        o[2] = -wk * (inv[3] * x + inv[1] * y + inv[4] * z);
+        o[3] = -wk * (inv[5] * x + inv[4] * y + inv[2] * z);
     }
 }
 
@@ -704,13 +838,30 @@ cudaError_t launch_lme_only(const double *node_x, const double *mp_x, int64_t nm
                             const int32_t *counts, int S, double beta, double tol_abs, int max_newton, double *lam,
                             double *shape, int32_t *iters, int32_t *status, cudaStream_t s)
 {
-    const size_t smem = search_lme_smem_bytes(S, kSearchWarps);
-    const unsigned blocks = (unsigned)((nm + kSearchWarps - 1) / kSearchWarps);
+    const size_t smem = lme_smem_bytes(S, kLmeWarps);
+    const unsigned blocks = (unsigned)((nm + kLmeWarps - 1) / kLmeWarps);
     if (blocks == 0) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(k_lme_only, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_lme_only<<<blocks, kSearchWarps * kWarp, smem, s>>>(node_x, mp_x, nm, ids, counts, S, beta, tol_abs,
-                                                          max_newton, lam, shape, iters, status);
+    k_lme_only<<<blocks, kLmeWarps * kWarp, smem, s>>>(node_x, mp_x, nm, ids, counts, S, beta, tol_abs, max_newton,
+                                                       lam, shape, iters, status);
+    return cudaGetLastError();
+}
+
+// self-test of the table-driven exponential against CUDA's exp
+__global__ void k_exp_selftest(const double *x, int64_t n, double *mine, double *ref)
+{
+    __shared__ double T[64];
+    exp_table_fill(T);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        mine[i] = exp_tang(x[i], T);
+        ref[i] = exp(x[i]);
+    }
+}
+
+cudaError_t launch_exp_selftest(const double *x, int64_t n, double *mine, double *ref, cudaStream_t s)
+{
+    k_exp_selftest<<<152 * 4, 256, 0, s>>>(x, n, mine, ref);
     return cudaGetLastError();
 }
 

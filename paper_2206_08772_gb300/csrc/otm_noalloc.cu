@@ -9,7 +9,7 @@
 // outputs; only the scratch is provided here.
 //
 // The static array below lives in every GPU that loads this library, from module load until
-// process exit (14 MiB). In host code its name is only a host-side stand-in, so the device
+// process exit (16 MiB). In host code its name is only a host-side stand-in, so the device
 // address is looked up once per device with cudaGetSymbolAddress while that device is current,
 // and that address is what the kernels receive.
 #include <mutex>
@@ -18,7 +18,7 @@
 
 namespace otm {
 
-constexpr size_t kNoallocScratchBytes = (size_t)14 << 20;
+constexpr size_t kNoallocScratchBytes = (size_t)16 << 20;
 constexpr int kNoallocMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];

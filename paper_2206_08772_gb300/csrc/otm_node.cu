@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(kNodeWarps * kWarp) k_node_update(const Dev D,
     if (MIXED) {
         long long sm = 0, sx = 0, sy = 0, sz = 0;
         for (int k = lane; k < L; k += kWarp) {
-            const float4 c = D.contrib32[D.perm[b + k]];
+            const float4 c = D.contrib32[b + k];
             sm += to_fixed64(c.x, em);
             sx += to_fixed64(c.y, ef);
             sy += to_fixed64(c.z, ef);
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(kNodeWarps * kWarp) k_node_update(const Dev D,
     } else {
         I128 sm = {0, 0}, sx = {0, 0}, sy = {0, 0}, sz = {0, 0};
         for (int k = lane; k < L; k += kWarp) {
-            const double4_32a c = D.contrib64[D.perm[b + k]];
+            const double4_32a c = D.contrib64[b + k];
             add128(sm, to_fixed128(c.x, em));
             add128(sx, to_fixed128(c.y, ef));
             add128(sy, to_fixed128(c.z, ef));

@@ -142,3 +142,23 @@ def test_return_map_vs_oracle(orc, otm, model):
     assert rel(T_g, np.array([r[4] for r in ref])) <= 1e-10
     assert np.array_equal(failed.astype(bool), np.array([r[6] for r in ref]))
     assert (eb_g > ebar).any()     # the sample crosses the yield surface
+
+
+def test_internal_exp_against_cuda_exp():
+    """The LME weights use the library's table-driven FP64 exp (Tang 1989); it must agree with
+    CUDA's exp to a few ulps over the whole range it serves."""
+    import ctypes as C
+    import paper_2206_08772_gb300 as g
+    L = g.load()
+    rng = np.random.default_rng(11)
+    x = np.concatenate([rng.uniform(-700, 700, 200000), rng.uniform(-40, 5, 800000),
+                        np.arange(-64, 65) * np.log(2) / 64, [0.0, -0.0, 1e-300, -1e-300, 700.0, -700.0]])
+    xt = torch.from_numpy(x).cuda()
+    mine, ref = torch.empty_like(xt), torch.empty_like(xt)
+    assert L.otm_exp_selftest(C.c_void_p(xt.data_ptr()), x.size, C.c_void_p(mine.data_ptr()),
+                              C.c_void_p(ref.data_ptr()), C.c_void_p(torch.cuda.current_stream().cuda_stream)) == 0
+    torch.cuda.synchronize()
+    m, r = mine.cpu().numpy(), ref.cpu().numpy()
+    relerr = np.abs(m - r) / r
+    assert relerr.max() <= 4.5e-16, relerr.max()
+    assert np.abs(m - np.exp(x)).max() / 1.0 <= np.abs(np.exp(x)).max() * 1e-15
