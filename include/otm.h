@@ -159,7 +159,8 @@ enum {
     OTM_PHASE_SEARCH = 4,        /* Algorithm 3 steps 2-3: supports, influence counts */
     OTM_PHASE_NODE_MAJOR = 5,    /* influence-list offsets (scan of the counts) */
     OTM_PHASE_LME = 6,           /* Eq. 14 + per-pair contributions in node-major order */
-    OTM_N_PHASES = 7
+    OTM_PHASE_COMPACT = 7,       /* erosion (Sec. 4.2 fracture) and orphan-node removal */
+    OTM_N_PHASES = 8
 };
 int otm_phase_timing(otm_handle *h, int32_t enable);
 int otm_phase_times(otm_handle *h, double *ms, int64_t *launches);

@@ -23,7 +23,8 @@
  *   - yield check on the deviatoric trial stress; Simo exponential-map radial return
  *   - JC rate term uses max(rate/rate0, 1); T* clamped to [0, 1]
  *   - heating dT = chi * q * d(ebar) / (rho0 cp), isothermal split (flow stress uses T_n)
- *   - fracture: ebar >= eps_f checked only where ebar > 0; eta = (tr sigma / 3) / sigma_v
+ *   - fracture: ebar >= eps_f checked only where ebar > 0; eta = (tr sigma / 3) / sigma_v, and
+ *     eta = sign(p) * infinity where sigma_v <= 1e-12 |p| (no deviatoric stress left)
  *   - wall contact projects the node onto the plane, keeping the tangential increment
  *   - tool contact: normal projection plus Coulomb stick/slip at the penalty limit m/dt^2
  */
@@ -488,12 +489,17 @@ static int return_map(const orc_material *M, double dt, const double dF[3][3], c
     o->eps_f = INFINITY;
     if (M->model == 1 && M->fracture && o->ebar > 0.0) {   /* Eq. JC-fracture */
         double p = K * tr / J;                /* (1/3) tr sigma */
-        double sv = q / J;                    /* von Mises Cauchy stress */
-        double eta = (sv > 0.0) ? p / sv : 0.0;
+        double sv = (q > 0.0 ? q : 0.0) / J;  /* von Mises Cauchy stress */
+        /* eta = p / sigma_v; with (numerically) no deviatoric stress, e.g. a melted point with
+         * zero flow stress, the triaxiality takes its limit sign(p) * infinity */
+        double eta;
+        if (sv > 1e-12 * fabs(p)) eta = p / sv;
+        else eta = (p > 0.0) ? INFINITY : ((p < 0.0) ? -INFINITY : 0.0);
+        double texp = (M->d3 == 0.0) ? 1.0 : exp(M->d3 * eta);
         double rstar = o->rate / M->eps_dot0;
         double lr = (rstar > 1.0) ? log(rstar) : 0.0;
         double tstar = clamp01((o->T - M->T_room) / (M->T_melt - M->T_room));
-        o->eps_f = (M->d1 + M->d2 * exp(M->d3 * eta)) * (1.0 + M->d4 * lr) * (1.0 + M->d5 * tstar);
+        o->eps_f = (M->d1 + M->d2 * texp) * (1.0 + M->d4 * lr) * (1.0 + M->d5 * tstar);
         o->failed = (o->ebar >= o->eps_f);
     }
     return ORC_OK;

@@ -22,7 +22,7 @@ ERR_NAMES = {0: "OK", -1: "ARG", -2: "CUDA", -3: "WORKSPACE", -4: "LME_NOCONV", 
 
 PRECISION_FP64, PRECISION_MIXED = 0, 1
 
-PHASES = ["node_update", "kinematics", "return_map", "grid", "search", "node_major", "lme"]
+PHASES = ["node_update", "kinematics", "return_map", "grid", "search", "node_major", "lme", "compact"]
 
 FIELD = dict(node_x=0, node_du=1, node_mass=2, node_force=3, mp_x=4, F=5, be=6, sigma=7, vol=8,
              ebar=9, T=10, lam=11, support_count=12, support_ids=13, shape=14, newton_it=15,

@@ -22,6 +22,7 @@ struct otm_handle {
     int32_t *scan_tmp;
     int64_t step;
     long long launches;
+    int64_t n_eroded, n_removed;
     // phase timing
     bool timing;
     struct Rec {
@@ -94,7 +95,7 @@ static size_t layout(int64_t nn, int64_t nm, int S, int precision, char *base, D
     TAKE(d.sorted, int32_t, nn);
     TAKE(d.cell_count, int32_t, (int64_t)max_cells + 1);
     TAKE(d.cell_start, int32_t, (int64_t)max_cells + 1);
-    TAKE(tmp, int32_t, scan_tmp_ints(nn + 1));
+    TAKE(tmp, int32_t, scan_tmp_ints((nn > nm ? nn : nm) + 1));
     // material points
     TAKE(d.xp, double4_32a, nm);
     TAKE(d.F, double, 9 * nm);
@@ -307,9 +308,21 @@ static int enqueue_step(otm_handle *h)
         PhaseScope ps(h, OTM_PHASE_RETURN_MAP);
         CK(launch_return_map(D, s, &h->launches));
     }
+    int64_t eroded = 0;
+    if (D.allow_erode) {   // fracture: failed MPs leave before the new supports are built
+        PhaseScope ps(h, OTM_PHASE_COMPACT);
+        CK(erode_mps(D, h->scan_tmp, &eroded, s, &h->launches));
+        h->n_eroded += eroded;
+    }
     // 5-6: linked-cell search, LME shape functions, contributions, node-major lists
     int rc = rebuild_supports(h);
     if (rc != OTM_OK) return rc;
+    if (eroded > 0) {      // nodes left in no support are removed
+        PhaseScope ps(h, OTM_PHASE_COMPACT);
+        int64_t removed = 0;
+        CK(remove_orphan_nodes(D, h->scan_tmp, &removed, s, &h->launches));
+        h->n_removed += removed;
+    }
     h->step++;
     return OTM_OK;
 }

@@ -229,6 +229,9 @@ bool carve_search_scratch(void *base, size_t bytes, int64_t nn, SearchScratch *S
 cudaError_t build_search_grid(const double *node_x, int64_t nn, double cell, SearchScratch *S,
                               double *grid_out, cudaStream_t s);
 size_t lme_smem_bytes(int S, int warps);
+cudaError_t erode_mps(Dev &D, int32_t *scan_tmp, int64_t *n_drop_host, cudaStream_t s, long long *launches);
+cudaError_t remove_orphan_nodes(Dev &D, int32_t *scan_tmp, int64_t *n_drop_host, cudaStream_t s,
+                                long long *launches);
 
 // stand-alone entry points reuse these
 cudaError_t launch_search_only(const double *node_x, int64_t nn, const double *mp_x, int64_t nm,

@@ -667,12 +667,14 @@ __device__ int return_map_point(const otm_material &M, double dt, const RmIn &in
     out.failed = false;
     if (M.model == 1 && M.fracture && out.ebar > 0.0) {
         const double pr = K * tr * iJ;
-        const double sv = qn * iJ;
-        const double eta = (sv > 0.0) ? pr / sv : 0.0;
+        const double sv = fmax(qn, 0.0) * iJ;
+        // triaxiality; its limit sign(p) * inf where no deviatoric stress is left (melted point)
+        const double eta = (sv > 1e-12 * fabs(pr)) ? pr / sv : (pr > 0.0 ? INFINITY : (pr < 0.0 ? -INFINITY : 0.0));
+        const double texp = (M.d3 == 0.0) ? 1.0 : exp(M.d3 * eta);
         const double rstar = out.rate / M.eps_dot0;
         const double lr = (rstar > 1.0) ? log(rstar) : 0.0;
         const double tstar = fmin(fmax((out.T - M.T_room) / (M.T_melt - M.T_room), 0.0), 1.0);
-        const double ef = (M.d1 + M.d2 * exp(M.d3 * eta)) * (1.0 + M.d4 * lr) * (1.0 + M.d5 * tstar);
+        const double ef = (M.d1 + M.d2 * texp) * (1.0 + M.d4 * lr) * (1.0 + M.d5 * tstar);
         out.failed = (out.ebar >= ef);
     }
     for (int c = 0; c < 6; c++)

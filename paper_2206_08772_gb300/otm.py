@@ -143,20 +143,25 @@ class OTM:
 
     # -- state transfer (host copies, ID order)
     def get(self, name: str, out: np.ndarray | None = None) -> np.ndarray:
-        c = self.counts() if name in ("support_ids", "shape") else None
+        c = None
         if name == "support_ids":
-            shape, dt = (self.n_mps, self.S), np.int32
+            shape, dt = (self.counts()["n_mps"], self.S), np.int32
         elif name == "shape":
-            shape, dt = (self.n_mps, self.S, 4), np.float64
+            shape, dt = (self.counts()["n_mps"], self.S, 4), np.float64
         else:
             w, dt = _WIDTH[name]
-            rows = self.n_nodes if name.startswith("node") else self.n_mps
+            c = self.counts()
+            rows = c["n_nodes"] if name.startswith("node") else c["n_mps"]
             shape = (rows, w) if w > 1 else (rows,)
         if out is None:
             out = np.empty(shape, dtype=dt)
         check(_lib.load().otm_state(self._h, FIELD[name], _ptr(out), out.nbytes), f"otm_state({name})")
         del c
         return out
+
+    def n_current(self):
+        c = self.counts()
+        return c["n_nodes"], c["n_mps"]
 
     def set(self, name: str, value: np.ndarray):
         w, dt = _WIDTH[name]

@@ -116,3 +116,35 @@ def test_error_status_nonconvergence(OTM):
     assert code in (-4, -8)
     s2 = OTM(p)
     assert s2.step(2) == 0
+
+
+def chip_case(embed_h):
+    h = 0.02e-3
+    return scenarios.chip_block(h=h, size=(0.4e-3, 0.2e-3, 0.1e-3), depth=0.06e-3, embed=embed_h * h, steps=8)
+
+
+@pytest.mark.parametrize("embed_h,steps", [(1.5, 6), (3.0, 8)])
+def test_chip_tool_contact_erosion_compaction(orc, OTM, embed_h, steps):
+    """Chip block with the rigid tool (Coulomb friction) embedded in the work piece: with
+    3 h of embedding the Johnson-Cook fracture criterion erodes material points from the second
+    step on and orphan nodes are removed; the GPU compaction must keep exactly the oracle's
+    survivors, in the same order, with matching supports and fields."""
+    p = chip_case(embed_h)
+    sim_o = orc.Sim(p)
+    sim_g = OTM(p, precision="fp64")
+    eroded = 0
+    for k in range(steps):
+        assert sim_o.step(1) == 0
+        assert sim_g.step(1) == 0, sim_g.error()
+        co, cg = sim_o.counts(), sim_g.counts()
+        assert (cg["n_mps"], cg["n_nodes"]) == (co["n_mps"], co["n_nodes"]), f"step {k + 1}"
+        assert np.array_equal(sim_g.get("mp_gid"), sim_o.get("mp_gid"))
+        assert np.array_equal(sim_g.get("node_gid"), sim_o.get("node_gid"))
+        assert supports_equal(sim_g, sim_o), f"step {k + 1}"
+        eroded = p.n_mps - co["n_mps"]
+    errs, bad = compare(sim_g, sim_o, {"default": 1e-10})
+    print("chip", embed_h, eroded, errs)
+    assert not bad, bad
+    if embed_h >= 3.0:
+        assert eroded > 100
+        assert sim_o.counts()["n_nodes"] < p.n_nodes

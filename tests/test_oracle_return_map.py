@@ -161,3 +161,17 @@ def test_jc_fracture_strain_from_cauchy_stress(orc):
         ef = (d1 + d2 * math.exp(d3 * eta)) * (1 + d4 * math.log(max(rate, 1))) * (1 + d5 * tstar)
         assert failed and abs(eb - ef) <= 1e-9 * ef
         assert (eta > 0) == (a > 1)
+
+
+def test_jc_fracture_of_melted_point_follows_pressure_sign(orc):
+    """Above the melting temperature the flow stress vanishes, so no deviatoric stress is left and
+    the triaxiality p / sigma_v is taken at its limit sign(p) * inf: hydrostatic tension fails
+    (eps_f -> d1 (...) < 0), hydrostatic compression does not (eps_f -> +inf)."""
+    m = scenarios.ti64_jc()
+    for a, want in ((1.002, True), (0.998, False)):
+        s = 1.05
+        F = np.diag([s * a, a / math.sqrt(s), a / math.sqrt(s)])
+        st, sig, be, eb, T, q, failed = orc.return_map(m, 1e-9, F, I6, 0.0, m.T_melt + 50.0, np.linalg.det(F))
+        assert st == 0 and eb > 0
+        assert abs(q) <= 1e-6 * m.E
+        assert failed == want
