@@ -107,6 +107,21 @@ def lib():
             L.orc_sim_set.argtypes = [_P, C.c_int32, _P, C.c_int64]
             L.orc_sim_refresh.restype = C.c_int
             L.orc_sim_refresh.argtypes = [_P]
+            L.orc_lme_backward.restype = C.c_int
+            L.orc_lme_backward.argtypes = [C.c_int64, _P, _P, _P, _P, C.c_double, _P, _P, _P]
+            L.orc_return_map_backward.restype = C.c_int
+            L.orc_return_map_backward.argtypes = [_P, C.c_double, _P, _P, C.c_double, C.c_double, C.c_double,
+                                                  _P, _P, C.c_double, C.c_double, _P, _P, _P, _P, _P, _P]
+            L.orc_sim_clone.restype = _P
+            L.orc_sim_clone.argtypes = [_P]
+            L.orc_adj_create.restype = _P
+            L.orc_adj_create.argtypes = [_P, _P]
+            L.orc_adj_destroy.restype = None
+            L.orc_adj_destroy.argtypes = [_P]
+            L.orc_adj_result.restype = None
+            L.orc_adj_result.argtypes = [_P, _P, _P]
+            L.orc_adjoint_step.restype = C.c_int
+            L.orc_adjoint_step.argtypes = [_P, _P, _P]
             assert L.orc_sizeof_params() == C.sizeof(Params)
             assert L.orc_sizeof_material() == C.sizeof(Material)
             _lib = L
@@ -179,6 +194,38 @@ def return_map(mat, dt: float, dF: np.ndarray, be_n: np.ndarray, ebar_n: float, 
     st = lib().orc_return_map(C.byref(m), dt, _ptr(dF), _ptr(be_n), ebar_n, T_n, J, _ptr(sig), _ptr(be),
                               C.byref(eb), C.byref(T), C.byref(q), C.byref(failed))
     return st, sig, be, eb.value, T.value, q.value, bool(failed.value)
+
+
+def lme_backward(d, N, G, lam, beta, Nb, Gb):
+    """Adjoint of the LME shape functions of one point: dL/dd given dL/dN and dL/d(grad N)."""
+    d = np.ascontiguousarray(d, np.float64)
+    N = np.ascontiguousarray(N, np.float64)
+    G = np.ascontiguousarray(G, np.float64)
+    lam = np.ascontiguousarray(lam, np.float64)
+    Nb = np.ascontiguousarray(Nb, np.float64)
+    Gb = np.ascontiguousarray(Gb, np.float64)
+    db = np.zeros_like(d)
+    st = lib().orc_lme_backward(d.shape[0], _ptr(d), _ptr(N), _ptr(G), _ptr(lam), beta, _ptr(Nb), _ptr(Gb), _ptr(db))
+    if st != OK:
+        raise RuntimeError(f"lme_backward {st}")
+    return db
+
+
+def return_map_backward(mat, dt, dF, be_n, ebar_n, T_n, J, sigb, beb, ebb, Tb):
+    """Adjoint of one MP's return map. Returns (dFb 3x3, be_nb 6, ebar_nb, T_nb, Jb, thetab 5)."""
+    m = material_struct(mat) if not isinstance(mat, Material) else mat
+    dF = np.ascontiguousarray(dF, np.float64).reshape(9)
+    be_n = np.ascontiguousarray(be_n, np.float64)
+    sigb = np.ascontiguousarray(sigb, np.float64)
+    beb = np.ascontiguousarray(beb, np.float64)
+    dFb, be_nb, thb = np.zeros(9), np.zeros(6), np.zeros(5)
+    ebn, Tn, Jb = C.c_double(0), C.c_double(0), C.c_double(0)
+    st = lib().orc_return_map_backward(C.byref(m), dt, _ptr(dF), _ptr(be_n), ebar_n, T_n, J, _ptr(sigb), _ptr(beb),
+                                       ebb, Tb, _ptr(dFb), _ptr(be_nb), C.byref(ebn), C.byref(Tn), C.byref(Jb),
+                                       _ptr(thb))
+    if st != OK:
+        raise RuntimeError(f"return_map_backward {st}")
+    return dFb.reshape(3, 3), be_nb, ebn.value, Tn.value, Jb.value, thb
 
 
 def search(node_x: np.ndarray, mp_x: np.ndarray, rs2: float, cell_size: float, cap: int | None = None):
@@ -298,3 +345,67 @@ class Sim:
 
     def refresh(self) -> int:
         return lib().orc_sim_refresh(self._h)
+
+    def clone(self) -> "Sim":
+        c = Sim.__new__(Sim)
+        c.prob, c.params = self.prob, self.params
+        c._h = lib().orc_sim_clone(self._h)
+        if not c._h:
+            raise MemoryError("oracle clone failed")
+        return c
+
+
+# ------------------------------------------------------------------ reference adjoint
+
+THETA_NAMES = ("A", "B", "n", "C", "m", "v0")
+
+
+def objectives(x: np.ndarray, node_mass: np.ndarray, h: float):
+    """Final rod length (max z over nodes with mass) and footprint radius (max radial distance
+    over nodes within 1e-3 h of the wall), with the arg-max nodes and d(objective)/d(x)."""
+    act = np.nonzero(node_mass > 0)[0]
+    i_len = int(act[np.argmax(x[act, 2])])
+    foot = np.nonzero(x[:, 2] <= 1e-3 * h)[0]
+    rad = np.sqrt(x[foot, 0] ** 2 + x[foot, 1] ** 2)
+    i_rad = int(foot[np.argmax(rad)])
+    L = float(x[i_len, 2])
+    R = float(np.sqrt(x[i_rad, 0] ** 2 + x[i_rad, 1] ** 2))
+    gL = np.zeros_like(x)
+    gL[i_len, 2] = 1.0
+    gR = np.zeros_like(x)
+    gR[i_rad, 0] = x[i_rad, 0] / R
+    gR[i_rad, 1] = x[i_rad, 1] / R
+    return (L, R), (gL, gR), (i_len, i_rad)
+
+
+def reference_adjoint(prob, steps: int):
+    """FP64 CPU reverse-mode gradients of (final length, footprint radius) with respect to
+    (A, B, n, C, m, v0), topology / contact set / plastic set frozen at the base trajectory.
+    Returns (values, gradients [2 x 6], arg-max nodes)."""
+    L = lib()
+    sims = [Sim(prob)]
+    for _ in range(steps):
+        nxt = sims[-1].clone()
+        st = nxt.step(1)
+        if st != OK:
+            raise RuntimeError(f"oracle step failed: {st}")
+        sims.append(nxt)
+    xK = sims[-1].get("node_x")
+    vals, seeds, argm = objectives(xK, sims[-1].get("node_mass"), prob.h)
+    grads = np.zeros((2, 6))
+    for o, seed in enumerate(seeds):
+        seed = np.ascontiguousarray(seed)
+        a = L.orc_adj_create(sims[-1]._h, _ptr(seed))
+        try:
+            for k in range(steps - 1, -1, -1):
+                st = L.orc_adjoint_step(sims[k]._h, sims[k + 1]._h, a)
+                if st != OK:
+                    raise RuntimeError(f"adjoint step {k} failed: {st}")
+            thb = np.zeros(5)
+            dub = np.zeros((sims[0].counts()["n_nodes"], 3))
+            L.orc_adj_result(a, _ptr(thb), _ptr(dub))
+        finally:
+            L.orc_adj_destroy(a)
+        grads[o, :5] = thb
+        grads[o, 5] = -prob.dt * dub[:, 2].sum()   # du_0 = (0, 0, -v0 dt) on every node
+    return vals, grads, argm

@@ -1010,3 +1010,528 @@ void orc_kinematics(int64_t n, const int32_t *ids, const double *N, const double
 
 int orc_sizeof_params(void) { return (int)sizeof(orc_params); }
 int orc_sizeof_material(void) { return (int)sizeof(orc_material); }
+
+/* ================================================================ reference adjoint (test oracle)
+ * Reverse-mode derivative of the explicit step (Algorithm 1) with frozen topology: supports,
+ * wall-contact set and the elastic/plastic branch of each return map are those of the base
+ * trajectory. Objectives are functions of the final node positions; parameters are the
+ * Johnson-Cook constants (A, B, n, C, m) of material 0 and the impact velocity (through the
+ * initial increments). Derivations:
+ *  - LME (Eq. 14), implicit-function theorem on r(lambda, d) = sum N_a d_a = 0:
+ *      grad N_a = -N_a H^-1 d_a, H = sum N d d^T - r r^T; dlambda = -H^-1 sum_a (dr/dd_a) dd_a,
+ *      dr/dd_a = N_a [1 + d_a (lambda - 2 beta d_a)^T] (at r = 0); N = softmax(f),
+ *      f_a = -beta |d_a|^2 + lambda . d_a.
+ *  - return map (Sec. 4): isotropic tensor functions of b_tr; principal derivatives by the chain
+ *    rule of the radial return (implicit function theorem on the consistency condition), the
+ *    off-diagonal part by divided differences (tau_A - tau_B)/(lam_A - lam_B), replaced by the
+ *    second-order symmetric limit when the eigenvalues (nearly) coincide.
+ *  - kinematics, lumped mass / force and the central-difference update: transposes of the
+ *    linear maps (the wall projection acts on the frozen contact set). */
+
+orc_sim *orc_sim_clone(const orc_sim *s)
+{
+    orc_sim *c = calloc(1, sizeof(orc_sim));
+    if (!c) return NULL;
+    *c = *s;
+#define CP(f, n) do { size_t b_ = (size_t)(n) * sizeof(*s->f); c->f = malloc(b_ ? b_ : 1); if (b_) memcpy(c->f, s->f, b_); } while (0)
+    CP(x, 3 * s->nn); CP(x_prev, 3 * s->nn); CP(du, 3 * s->nn); CP(mI, s->nn); CP(rI, 3 * s->nn);
+    CP(flags, s->nn); CP(node_gid, s->nn);
+    CP(xp, 3 * s->nm); CP(xp_prev, 3 * s->nm); CP(F, 9 * s->nm); CP(dF, 9 * s->nm); CP(be, 6 * s->nm);
+    CP(sig, 6 * s->nm); CP(vol, s->nm); CP(mass, s->nm); CP(ebar, s->nm); CP(T, s->nm); CP(rate, s->nm);
+    CP(lam, 3 * s->nm); CP(mat, s->nm); CP(newton_it, s->nm); CP(mp_gid, s->nm); CP(failed, s->nm);
+    CP(off, s->nm + 1); CP(ids, s->n_pairs); CP(N, s->n_pairs); CP(dN, 3 * s->n_pairs);
+#undef CP
+    c->cap_pairs = s->n_pairs;
+    c->cap_nodes = s->nn;
+    c->cap_mps = s->nm;
+    return c;
+}
+
+/* ---------------------------------------------------------------- LME backward (one MP) */
+/* Inputs: d (n x 3) = x_p - x_a, N, G (n x 3) = grad N, lambda, beta; adjoints Nb, Gb.
+ * Output: db (n x 3) = dL/dd_a. */
+int orc_lme_backward(int64_t n, const double *d, const double *N, const double *G, const double *lam, double beta,
+                     const double *Nb_in, const double *Gb, double *db)
+{
+    (void)G;   /* grad N is recomputed from H below */
+    double H[3][3] = {{0}}, r[3] = {0, 0, 0}, Hi[3][3];
+    for (int64_t a = 0; a < n; a++)
+        for (int i = 0; i < 3; i++) {
+            r[i] += N[a] * d[3 * a + i];
+            for (int j = 0; j < 3; j++) H[i][j] += N[a] * d[3 * a + i] * d[3 * a + j];
+        }
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) H[i][j] -= r[i] * r[j];
+    if (!inv3(H, Hi)) return ORC_ERR_LME_NOCONV;
+    double *Nb = malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+    if (!Nb) return ORC_ERR_OOM;
+    /* G_a = -N_a u_a, u_a = H^-1 d_a */
+    double Hb[3][3] = {{0}};
+    for (int64_t a = 0; a < n; a++) {
+        const double *da = d + 3 * a, *gb = Gb + 3 * a;
+        double u[3], w[3];
+        for (int i = 0; i < 3; i++) u[i] = Hi[i][0] * da[0] + Hi[i][1] * da[1] + Hi[i][2] * da[2];
+        Nb[a] = Nb_in[a] - (gb[0] * u[0] + gb[1] * u[1] + gb[2] * u[2]);
+        for (int i = 0; i < 3; i++) w[i] = -N[a] * (Hi[i][0] * gb[0] + Hi[i][1] * gb[1] + Hi[i][2] * gb[2]);
+        for (int i = 0; i < 3; i++) {
+            db[3 * a + i] = w[i];
+            for (int j = 0; j < 3; j++) Hb[i][j] -= w[i] * u[j];
+        }
+    }
+    double Hs[3][3];
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) Hs[i][j] = 0.5 * (Hb[i][j] + Hb[j][i]);
+    /* H = sum N d d^T - r r^T with r = sum N d (r ~ 0 at convergence; kept for consistency) */
+    double Hr[3] = {0, 0, 0};   /* Hs r */
+    for (int i = 0; i < 3; i++) Hr[i] = Hs[i][0] * r[0] + Hs[i][1] * r[1] + Hs[i][2] * r[2];
+    double S = 0.0;
+    for (int64_t a = 0; a < n; a++) {
+        const double *da = d + 3 * a;
+        double Hd[3];
+        for (int i = 0; i < 3; i++) Hd[i] = Hs[i][0] * da[0] + Hs[i][1] * da[1] + Hs[i][2] * da[2];
+        /* from sum N d d^T and from -r r^T (r = sum N d): d r r^T -> rbar = -2 Hs r */
+        Nb[a] += (da[0] * Hd[0] + da[1] * Hd[1] + da[2] * Hd[2]) - 2.0 * (da[0] * Hr[0] + da[1] * Hr[1] + da[2] * Hr[2]);
+        for (int i = 0; i < 3; i++) db[3 * a + i] += 2.0 * N[a] * Hd[i] - 2.0 * N[a] * Hr[i];
+        S += N[a] * Nb[a];
+    }
+    /* softmax: fbar_a = N_a (Nb_a - S); f_a = -beta |d|^2 + lambda.d */
+    double lb[3] = {0, 0, 0};
+    for (int64_t a = 0; a < n; a++) {
+        const double *da = d + 3 * a;
+        double fb = N[a] * (Nb[a] - S);
+        for (int i = 0; i < 3; i++) {
+            db[3 * a + i] += fb * (lam[i] - 2.0 * beta * da[i]);
+            lb[i] += fb * da[i];
+        }
+    }
+    /* lambda(d) from r = 0: mu = H^-1 lb, db_a -= N_a [mu + (lambda - 2 beta d_a)(d_a . mu)] */
+    double mu[3];
+    for (int i = 0; i < 3; i++) mu[i] = Hi[i][0] * lb[0] + Hi[i][1] * lb[1] + Hi[i][2] * lb[2];
+    for (int64_t a = 0; a < n; a++) {
+        const double *da = d + 3 * a;
+        double dm = da[0] * mu[0] + da[1] * mu[1] + da[2] * mu[2];
+        for (int i = 0; i < 3; i++) db[3 * a + i] -= N[a] * (mu[i] + (lam[i] - 2.0 * beta * da[i]) * dm);
+    }
+    free(Nb);
+    return ORC_OK;
+}
+
+/* ---------------------------------------------------------------- return map with tangents */
+typedef struct {
+    double K, mu, dt;
+    double lam[3], Q[3][3], eps[3], e[3], enorm, qtr, x, q, rho, ee[3], tau[3], bA[3];
+    int plastic, heating;
+    double dsy_debar, dsy_dx, dsy_dT, dsy_dth[5], chi_c;   /* sigma_Y partials, chi/(rho0 cp) */
+    double J;
+} rm_detail_t;
+
+/* JC partials at (ebar_n + x, x/dt, T) with respect to ebar_n, x (total), T and (A, B, n, C, m) */
+static void jc_partials(const orc_material *M, double ebar_n, double x, double dt, double T, double *sy,
+                        double *d_eb, double *d_x, double *d_T, double d_th[5])
+{
+    double ebar = ebar_n + x;
+    double span = M->T_melt - M->T_room;
+    double tstar_raw = (T - M->T_room) / span;
+    double tstar = clamp01(tstar_raw);
+    double therm = 1.0 - pow(tstar, M->m);
+    double dtherm_dT = (tstar_raw > 0.0 && tstar_raw < 1.0) ? -M->m * pow(tstar, M->m - 1.0) / span : 0.0;
+    double rstar = (x / dt) / M->eps_dot0;
+    double rate = 1.0, drate_dx = 0.0, lr = 0.0;
+    if (rstar > 1.0) { lr = log(rstar); rate = 1.0 + M->C * lr; drate_dx = M->C / x; }
+    double epn = pow(ebar, M->n);
+    double hard = M->A + M->B * epn;
+    double dhard = (ebar > 0.0) ? M->B * M->n * pow(ebar, M->n - 1.0) : 0.0;
+    *sy = hard * rate * therm;
+    *d_eb = dhard * rate * therm;
+    *d_x = (dhard * rate + hard * drate_dx) * therm;
+    *d_T = hard * rate * dtherm_dT;
+    d_th[0] = rate * therm;                                        /* A */
+    d_th[1] = epn * rate * therm;                                  /* B */
+    d_th[2] = (ebar > 0.0) ? M->B * epn * log(ebar) * rate * therm : 0.0;   /* n */
+    d_th[3] = hard * lr * therm;                                   /* C */
+    d_th[4] = (tstar > 0.0) ? -hard * rate * pow(tstar, M->m) * log(tstar) : 0.0;   /* m */
+}
+
+static int rm_detail(const orc_material *M, double dt, const double dF[3][3], const double be_n[6], double ebar_n,
+                     double T_n, double J, rm_detail_t *o)
+{
+    rm_out_t out;
+    int st = return_map(M, dt, dF, be_n, ebar_n, T_n, J, &out);
+    if (st != ORC_OK) return st;
+    memset(o, 0, sizeof(*o));
+    o->K = M->E / (3.0 * (1.0 - 2.0 * M->nu));
+    o->mu = M->E / (2.0 * (1.0 + M->nu));
+    o->dt = dt;
+    o->J = J;
+    double b[3][3], t1[3][3], dFT[3][3], btr[3][3];
+    sym_to_full(be_n, b);
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) dFT[i][j] = dF[j][i];
+    matmul3(dF, b, t1);
+    matmul3(t1, dFT, btr);
+    for (int i = 0; i < 3; i++)
+        for (int j = i + 1; j < 3; j++) btr[i][j] = btr[j][i] = 0.5 * (btr[i][j] + btr[j][i]);
+    jacobi_eig3(btr, o->lam, o->Q);
+    double tr = 0.0;
+    for (int A = 0; A < 3; A++) { o->eps[A] = 0.5 * log(o->lam[A]); tr += o->eps[A]; }
+    double en2 = 0.0;
+    for (int A = 0; A < 3; A++) { o->e[A] = o->eps[A] - tr / 3.0; en2 += o->e[A] * o->e[A]; }
+    o->enorm = sqrt(en2);
+    o->qtr = sqrt(6.0) * o->mu * o->enorm;
+    o->x = out.ebar - ebar_n;
+    o->plastic = o->x > 0.0;
+    o->q = o->qtr - 3.0 * o->mu * o->x;
+    o->rho = o->plastic ? o->q / o->qtr : 1.0;
+    for (int A = 0; A < 3; A++) {
+        o->ee[A] = tr / 3.0 + o->e[A] * o->rho;
+        o->tau[A] = o->K * tr + 2.0 * o->mu * o->e[A] * o->rho;
+        o->bA[A] = exp(2.0 * o->ee[A]);
+    }
+    o->heating = (M->model == 1 && M->chi > 0.0 && o->plastic);
+    o->chi_c = o->heating ? M->chi / (M->rho0 * M->cp) : 0.0;
+    if (M->model == 0) {
+        o->dsy_debar = M->H;
+        o->dsy_dx = M->H;
+    } else {
+        double sy;
+        jc_partials(M, ebar_n, o->x, dt, T_n, &sy, &o->dsy_debar, &o->dsy_dx, &o->dsy_dT, o->dsy_dth);
+    }
+    return ORC_OK;
+}
+
+/* tangent of the principal map: inputs (dlam[3], debar_n, dT_n, dth[5]) ->
+ * outputs (dtau[3], db[3], debar', dT') */
+static void rm_principal_tangent(const rm_detail_t *o, const double dlam[3], double deb, double dT, const double dth[5],
+                                 double dtau[3], double db[3], double *deb1, double *dT1)
+{
+    double deps[3], dtr = 0.0, de[3], den = 0.0;
+    for (int A = 0; A < 3; A++) { deps[A] = dlam[A] / (2.0 * o->lam[A]); dtr += deps[A]; }
+    for (int A = 0; A < 3; A++) de[A] = deps[A] - dtr / 3.0;
+    if (o->enorm > 0.0)
+        for (int A = 0; A < 3; A++) den += o->e[A] * de[A] / o->enorm;
+    double dqtr = sqrt(6.0) * o->mu * den;
+    double dx = 0.0, drho = 0.0, dq = dqtr;
+    if (o->plastic) {
+        double dsyth = 0.0;
+        for (int k = 0; k < 5; k++) dsyth += o->dsy_dth[k] * dth[k];
+        dx = (dqtr - o->dsy_debar * deb - o->dsy_dT * dT - dsyth) / (3.0 * o->mu + o->dsy_dx);
+        dq = dqtr - 3.0 * o->mu * dx;
+        drho = (dq - o->rho * dqtr) / o->qtr;
+    }
+    for (int A = 0; A < 3; A++) {
+        double dee = dtr / 3.0 + de[A] * o->rho + o->e[A] * drho;
+        dtau[A] = o->K * dtr + 2.0 * o->mu * (de[A] * o->rho + o->e[A] * drho);
+        db[A] = 2.0 * o->bA[A] * dee;
+    }
+    *deb1 = deb + dx;
+    *dT1 = dT + o->chi_c * (dq * o->x + o->q * dx);
+}
+
+/* Backward of one MP's return map. sigb, beb: adjoints of the 6-vectors sigma', b' (d L / d
+ * component); ebb, Tb: adjoints of ebar', T'. Outputs: dFb (9, d L / d dF_ij), be_nb (6-vector),
+ * ebb_n, Tb_n, Jb (adjoint of J = det F'), thb (5, accumulated). */
+static void rm_backward(const rm_detail_t *o, const double dF[3][3], const double be_n[6], const double sig[6],
+                        const double sigb[6], const double beb[6], double ebb, double Tb, double dFb[3][3],
+                        double be_nb[6], double *ebb_n, double *Tb_n, double *Jb, double thb[5])
+{
+    /* full symmetric adjoints from 6-vector adjoints (off-diagonal entries count twice) */
+    double Sb[3][3], Bb[3][3], S[3][3];
+    sym_to_full(sigb, Sb); sym_to_full(beb, Bb); sym_to_full(sig, S);
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++)
+            if (i != j) { Sb[i][j] *= 0.5; Bb[i][j] *= 0.5; }
+    /* sigma = tau / J */
+    double taub[3][3], ss = 0.0;
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) { taub[i][j] = Sb[i][j] / o->J; ss += Sb[i][j] * S[i][j]; }
+    *Jb = -ss / o->J;
+    /* to the eigenbasis */
+    double Tq[3][3], Bq[3][3], tmp[3][3], QT[3][3];
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) QT[i][j] = o->Q[j][i];
+    matmul3(QT, taub, tmp); matmul3(tmp, o->Q, Tq);
+    matmul3(QT, Bb, tmp); matmul3(tmp, o->Q, Bq);
+    /* principal Jacobian columns: 3 eigenvalues, ebar_n, T_n, 5 parameters */
+    double col_tau[10][3], col_b[10][3], col_eb[10], col_T[10];
+    for (int c = 0; c < 10; c++) {
+        double dl[3] = {0, 0, 0}, deb = 0, dTt = 0, dth[5] = {0, 0, 0, 0, 0};
+        if (c < 3) dl[c] = 1.0;
+        else if (c == 3) deb = 1.0;
+        else if (c == 4) dTt = 1.0;
+        else dth[c - 5] = 1.0;
+        rm_principal_tangent(o, dl, deb, dTt, dth, col_tau[c], col_b[c], &col_eb[c], &col_T[c]);
+    }
+    double g[10];
+    for (int c = 0; c < 10; c++) {
+        g[c] = ebb * col_eb[c] + Tb * col_T[c];
+        for (int A = 0; A < 3; A++) g[c] += Tq[A][A] * col_tau[c][A] + Bq[A][A] * col_b[c][A];
+    }
+    /* eigenbasis adjoint of b_tr: diagonal from the principal chain, off-diagonal from divided
+     * differences (second-order symmetric limit for close eigenvalues) */
+    double Xb[3][3] = {{0}};
+    for (int A = 0; A < 3; A++) Xb[A][A] = g[A];
+    double lmax = fmax(fabs(o->lam[0]), fmax(fabs(o->lam[1]), fabs(o->lam[2])));
+    for (int A = 0; A < 3; A++)
+        for (int B = 0; B < 3; B++) {
+            if (A == B) continue;
+            double th_t, th_b;
+            double dl = o->lam[A] - o->lam[B];
+            if (fabs(dl) > 1e-6 * lmax) {
+                th_t = (o->tau[A] - o->tau[B]) / dl;
+                th_b = (o->bA[A] - o->bA[B]) / dl;
+            } else {
+                th_t = 0.5 * ((col_tau[A][A] - col_tau[B][A]) + (col_tau[B][B] - col_tau[A][B]));
+                th_b = 0.5 * ((col_b[A][A] - col_b[B][A]) + (col_b[B][B] - col_b[A][B]));
+            }
+            Xb[A][B] = th_t * Tq[A][B] + th_b * Bq[A][B];
+        }
+    double btrb[3][3];
+    matmul3(o->Q, Xb, tmp); matmul3(tmp, QT, btrb);
+    /* b_tr = dF b dF^T */
+    double b[3][3], dFT[3][3], t2[3][3];
+    sym_to_full(be_n, b);
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) dFT[i][j] = dF[j][i];
+    matmul3(btrb, dF, tmp); matmul3(tmp, b, t2);
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) dFb[i][j] = 2.0 * t2[i][j];
+    double bbf[3][3];
+    matmul3(dFT, btrb, tmp); matmul3(tmp, dF, bbf);
+    be_nb[0] = bbf[0][0]; be_nb[1] = bbf[1][1]; be_nb[2] = bbf[2][2];
+    be_nb[3] = bbf[0][1] + bbf[1][0]; be_nb[4] = bbf[1][2] + bbf[2][1]; be_nb[5] = bbf[0][2] + bbf[2][0];
+    *ebb_n = g[3];
+    *Tb_n = g[4];
+    for (int k = 0; k < 5; k++) thb[k] += g[5 + k];
+}
+
+/* stand-alone entry for tests: one MP */
+int orc_return_map_backward(const orc_material *M, double dt, const double *dF9, const double *be_n, double ebar_n,
+                            double T_n, double J, const double *sigb, const double *beb, double ebb, double Tb,
+                            double *dFb9, double *be_nb, double *ebb_n, double *Tb_n, double *Jb, double *thb)
+{
+    double dF[3][3];
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) dF[i][j] = dF9[3 * i + j];
+    rm_detail_t o;
+    int st = rm_detail(M, dt, dF, be_n, ebar_n, T_n, J, &o);
+    if (st != ORC_OK) return st;
+    rm_out_t out;
+    return_map(M, dt, dF, be_n, ebar_n, T_n, J, &out);
+    double Fb[3][3];
+    for (int k = 0; k < 5; k++) thb[k] = 0.0;
+    rm_backward(&o, dF, be_n, out.sig, sigb, beb, ebb, Tb, Fb, be_nb, ebb_n, Tb_n, Jb, thb);
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) dFb9[3 * i + j] = Fb[i][j];
+    return ORC_OK;
+}
+
+/* ---------------------------------------------------------------- whole-step adjoint */
+typedef struct {
+    int64_t nn, nm, np;
+    double *xb, *dub;               /* nodes: d L / d x, d L / d du of the current state */
+    double *Fb, *beb, *ebb, *Tb, *vb, *sigb;   /* MPs */
+    double *Nb, *Gb;                /* pairs of the current state's supports */
+    double thb[5];                  /* d L / d (A, B, n, C, m) of material 0 */
+} orc_adj;
+
+static void adj_free(orc_adj *a)
+{
+    free(a->xb); free(a->dub); free(a->Fb); free(a->beb); free(a->ebb); free(a->Tb); free(a->vb); free(a->sigb);
+    free(a->Nb); free(a->Gb);
+}
+
+static int adj_alloc(orc_adj *a, int64_t nn, int64_t nm, int64_t np)
+{
+    memset(a, 0, sizeof(*a));
+    a->nn = nn; a->nm = nm; a->np = np;
+    a->xb = calloc((size_t)(3 * nn + 1), 8); a->dub = calloc((size_t)(3 * nn + 1), 8);
+    a->Fb = calloc((size_t)(9 * nm + 1), 8); a->beb = calloc((size_t)(6 * nm + 1), 8);
+    a->ebb = calloc((size_t)(nm + 1), 8); a->Tb = calloc((size_t)(nm + 1), 8); a->vb = calloc((size_t)(nm + 1), 8);
+    a->sigb = calloc((size_t)(6 * nm + 1), 8);
+    a->Nb = calloc((size_t)(np + 1), 8); a->Gb = calloc((size_t)(3 * np + 1), 8);
+    if (!a->xb || !a->dub || !a->Fb || !a->beb || !a->ebb || !a->Tb || !a->vb || !a->sigb || !a->Nb || !a->Gb) {
+        adj_free(a);
+        return ORC_ERR_OOM;
+    }
+    return ORC_OK;
+}
+
+orc_adj *orc_adj_create(const orc_sim *s, const double *xb_seed)
+{
+    orc_adj *a = calloc(1, sizeof(orc_adj));
+    if (!a || adj_alloc(a, s->nn, s->nm, s->n_pairs) != ORC_OK) { free(a); return NULL; }
+    memcpy(a->xb, xb_seed, (size_t)(3 * s->nn) * 8);
+    return a;
+}
+
+void orc_adj_destroy(orc_adj *a)
+{
+    if (!a) return;
+    adj_free(a);
+    free(a);
+}
+
+void orc_adj_result(const orc_adj *a, double *thb, double *dub)
+{
+    memcpy(thb, a->thb, sizeof(a->thb));
+    if (dub) memcpy(dub, a->dub, (size_t)(3 * a->nn) * 8);
+}
+
+/* One step backward: a holds adjoints of state s1 (= step(s0)); on return, adjoints of s0.
+ * Requires: no erosion in the step (s0 and s1 have the same node and MP sets), J2 or JC. */
+int orc_adjoint_step(const orc_sim *s0, const orc_sim *s1, orc_adj *a)
+{
+    const orc_params *P = &s1->P;
+    if (s0->nn != s1->nn || s0->nm != s1->nm) return ORC_ERR_ARG;
+    const int64_t nn = s0->nn, nm = s0->nm;
+    const double dt = P->dt;
+    orc_adj o;   /* adjoints of s0 being built */
+    int st = adj_alloc(&o, nn, nm, s0->n_pairs);
+    if (st != ORC_OK) return st;
+    memcpy(o.thb, a->thb, sizeof(o.thb));
+    double *xpb = calloc((size_t)(3 * nm + 1), 8);        /* adjoint of x_p,n+1 */
+    double *xb1 = malloc((size_t)(3 * nn + 1) * 8);       /* adjoint of x_n+1 (total) */
+    double *dub1 = malloc((size_t)(3 * nn + 1) * 8);      /* adjoint of du_n+1 */
+    double *mb = calloc((size_t)(nn + 1), 8), *rb = calloc((size_t)(3 * nn + 1), 8);
+    double *d = malloc((size_t)4096 * 3 * 8), *db = malloc((size_t)4096 * 3 * 8);
+    if (!xpb || !xb1 || !dub1 || !mb || !rb || !d || !db) { st = ORC_ERR_OOM; goto done; }
+    memcpy(xb1, a->xb, (size_t)(3 * nn) * 8);
+    memcpy(dub1, a->dub, (size_t)(3 * nn) * 8);
+
+    /* (6)^T LME at the end of the step: shape of s1 from x_p,n+1 and x_n+1 */
+    for (int64_t p = 0; p < nm; p++) {
+        int64_t b0 = s1->off[p], n = s1->off[p + 1] - b0;
+        if (n > 4096) { st = ORC_ERR_CAPACITY; goto done; }
+        for (int64_t k = 0; k < n; k++)
+            for (int i = 0; i < 3; i++) d[3 * k + i] = s1->xp[3 * p + i] - s1->x[3 * (int64_t)s1->ids[b0 + k] + i];
+        st = orc_lme_backward(n, d, s1->N + b0, s1->dN + 3 * b0, s1->lam + 3 * p, P->beta, a->Nb + b0,
+                              a->Gb + 3 * b0, db);
+        if (st != ORC_OK) goto done;
+        for (int64_t k = 0; k < n; k++) {
+            int64_t id = s1->ids[b0 + k];
+            for (int i = 0; i < 3; i++) {
+                xpb[3 * p + i] += db[3 * k + i];
+                xb1[3 * id + i] -= db[3 * k + i];
+            }
+        }
+    }
+    /* (4)^T return map and (3)^T kinematics, per MP (shape of s0) */
+    for (int64_t p = 0; p < nm; p++) {
+        double D[3][3], Fo[3][3], Fn[3][3];
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) {
+                D[i][j] = s1->dF[9 * p + 3 * i + j];
+                Fo[i][j] = s0->F[9 * p + 3 * i + j];
+                Fn[i][j] = s1->F[9 * p + 3 * i + j];
+            }
+        double Jn = det3(Fn), detD = det3(D);
+        rm_detail_t det;
+        st = rm_detail(&P->mat[s0->mat[p]], dt, D, s0->be + 6 * p, s0->ebar[p], s0->T[p], Jn, &det);
+        if (st != ORC_OK) goto done;
+        double Db[3][3], Jb, ebn, Tn;
+        double thb_local[5] = {0, 0, 0, 0, 0};
+        rm_backward(&det, D, s0->be + 6 * p, s1->sig + 6 * p, a->sigb + 6 * p, a->beb + 6 * p, a->ebb[p], a->Tb[p],
+                    Db, o.beb + 6 * p, &ebn, &Tn, &Jb, thb_local);
+        if (s0->mat[p] == 0)
+            for (int k = 0; k < 5; k++) o.thb[k] += thb_local[k];
+        o.ebb[p] = ebn;
+        o.Tb[p] = Tn;
+        /* F' = dF F: Fb' total = Fb + Jb J F'^-T */
+        double Fni[3][3], Fbt[3][3], Di[3][3];
+        if (!inv3(Fn, Fni) || !inv3(D, Di)) { st = ORC_ERR_JACOBIAN; goto done; }
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) Fbt[i][j] = a->Fb[9 * p + 3 * i + j] + Jb * Jn * Fni[j][i];
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) {
+                double fo = 0.0, db_ = 0.0;
+                for (int k = 0; k < 3; k++) {
+                    fo += D[k][i] * Fbt[k][j];        /* dF^T Fb */
+                    db_ += Fbt[i][k] * Fo[j][k];      /* Fb F^T */
+                }
+                o.Fb[9 * p + 3 * i + j] = fo;
+                Db[i][j] += db_;
+            }
+        /* v' = det(dF) v */
+        double vnew = s1->vol[p];
+        o.vb[p] += detD * a->vb[p];
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) Db[i][j] += a->vb[p] * vnew * Di[j][i];
+        /* dF = 1 + sum du'_a (x) G_a ; x_p' = sum N_a x'_a  (s0 supports) */
+        for (int64_t k = s0->off[p]; k < s0->off[p + 1]; k++) {
+            int64_t id = s0->ids[k];
+            const double *g = s0->dN + 3 * k;
+            const double *u = s1->du + 3 * id;
+            for (int i = 0; i < 3; i++) {
+                dub1[3 * id + i] += Db[i][0] * g[0] + Db[i][1] * g[1] + Db[i][2] * g[2];
+                o.Gb[3 * k + i] += Db[0][i] * u[0] + Db[1][i] * u[1] + Db[2][i] * u[2];
+                xb1[3 * id + i] += s0->N[k] * xpb[3 * p + i];
+            }
+            o.Nb[k] += xpb[3 * p] * s1->x[3 * id] + xpb[3 * p + 1] * s1->x[3 * id + 1] + xpb[3 * p + 2] * s1->x[3 * id + 2];
+        }
+    }
+    /* (2)^T nodes: x' = P(x + du_t), du' = x' - x, du_t = du + dt^2 r / m */
+    for (int64_t i = 0; i < nn; i++) {
+        double *xb0 = o.xb + 3 * i, *dub0 = o.dub + 3 * i;
+        const double *xt1 = xb1 + 3 * i, *ut1 = dub1 + 3 * i;
+        if (s0->flags[i] & 1) {   /* fixed: x' = x, du' = 0 */
+            for (int c = 0; c < 3; c++) xb0[c] = xt1[c];
+            continue;
+        }
+        double m = s1->mI[i];
+        double dut[3], tot[3];
+        for (int c = 0; c < 3; c++) {
+            dut[c] = s0->du[3 * i + c] + ((m > 0.0) ? dt * dt * s1->rI[3 * i + c] / m : 0.0);
+            tot[c] = xt1[c] + ut1[c];
+        }
+        if (P->wall) {   /* frozen contact set: projection along n removes the normal part */
+            double g = 0.0, tn = 0.0;
+            for (int c = 0; c < 3; c++) g += (s0->x[3 * i + c] + dut[c] - P->wall_p[c]) * P->wall_n[c];
+            if (g < 0.0) {
+                for (int c = 0; c < 3; c++) tn += tot[c] * P->wall_n[c];
+                for (int c = 0; c < 3; c++) tot[c] -= tn * P->wall_n[c];
+            }
+        }
+        for (int c = 0; c < 3; c++) {
+            xb0[c] = tot[c] - ut1[c];
+            dub0[c] = tot[c];
+        }
+        if (m > 0.0) {
+            double rdot = 0.0;
+            for (int c = 0; c < 3; c++) {
+                rb[3 * i + c] = dt * dt / m * tot[c];
+                rdot += s1->rI[3 * i + c] * tot[c];
+            }
+            mb[i] = -dt * dt * rdot / (m * m);
+        }
+    }
+    /* (1)^T lumped mass and internal force (s0 supports, sigma_n, v_n) */
+    for (int64_t p = 0; p < nm; p++) {
+        const double *sg = s0->sig + 6 * p;
+        double S[3][3];
+        sym_to_full(sg, S);
+        double vp = s0->vol[p], mp = s0->mass[p];
+        double Sb[3][3] = {{0}};
+        for (int64_t k = s0->off[p]; k < s0->off[p + 1]; k++) {
+            int64_t id = s0->ids[k];
+            const double *g = s0->dN + 3 * k, *r_ = rb + 3 * id;
+            o.Nb[k] += mb[id] * mp;
+            for (int i = 0; i < 3; i++) {
+                double sg_i = S[i][0] * g[0] + S[i][1] * g[1] + S[i][2] * g[2];
+                o.vb[p] -= r_[i] * sg_i;
+                o.Gb[3 * k + i] -= vp * (S[0][i] * r_[0] + S[1][i] * r_[1] + S[2][i] * r_[2]);
+                for (int j = 0; j < 3; j++) Sb[i][j] -= vp * r_[i] * g[j];
+            }
+        }
+        double *sb = o.sigb + 6 * p;
+        sb[0] = Sb[0][0]; sb[1] = Sb[1][1]; sb[2] = Sb[2][2];
+        sb[3] = Sb[0][1] + Sb[1][0]; sb[4] = Sb[1][2] + Sb[2][1]; sb[5] = Sb[0][2] + Sb[2][0];
+    }
+    adj_free(a);
+    *a = o;
+    memset(&o, 0, sizeof(o));
+    st = ORC_OK;
+done:
+    if (st != ORC_OK) adj_free(&o);
+    free(xpb); free(xb1); free(dub1); free(mb); free(rb); free(d); free(db);
+    return st;
+}
