@@ -168,6 +168,35 @@ int otm_phase_times(otm_handle *h, double *ms, int64_t *launches);
 void otm_destroy(otm_handle *h);
 
 /* ---------------------------------------------------------------------------------------
+ * Snapshots and the adjoint (reverse mode). The adjoint differentiates functions of the final
+ * node positions with respect to the Johnson-Cook constants (A, B, n, C, m) of material 0 and
+ * the initial nodal increments, with the supports, the wall-contact set and each return map's
+ * elastic/plastic branch frozen at the trajectory being differentiated (no erosion). Paper:
+ * Eq. 4-14 and Sec. 4 define the step; the adjoint is their transpose (LME by the implicit-
+ * function theorem on sum N_a (x_p - x_a) = 0, the return map as isotropic tensor functions).
+ * ------------------------------------------------------------------------------------- */
+
+/* Bytes of one snapshot (device memory, 256-byte aligned, caller-owned). */
+int otm_snapshot_bytes(otm_handle *h, size_t *bytes);
+/* Copy the complete state into / from a snapshot (device to device). Loading regenerates the
+ * shape functions and node-major lists from the stored state, reproducing them exactly. */
+int otm_snapshot_save(otm_handle *h, void *dst);
+int otm_snapshot_load(otm_handle *h, const void *src);
+
+/* Bytes of the adjoint workspace (device memory, 256-byte aligned, caller-owned). */
+int otm_adjoint_bytes(otm_handle *h, size_t *bytes);
+/* Start a backward pass at the current (final) state: xbar_host (n_nodes x 3, host) is
+ * d objective / d node positions; every other adjoint starts at zero. */
+int otm_adjoint_begin(otm_handle *h, void *adj_ws, size_t bytes, const double *xbar_host);
+/* One backward step. Precondition: the handle holds state n (e.g. from otm_snapshot_load) and
+ * the adjoint workspace holds the adjoint of state n+1. The call recomputes step n (which is
+ * deterministic), then propagates the adjoint to state n. The handle then holds state n+1. */
+int otm_adjoint_step(otm_handle *h, void *adj_ws);
+/* theta_bar[5] = d objective / d (A, B, n, C, m); dubar_host (n_nodes x 3, optional) =
+ * d objective / d (displacement increments of the state the backward pass has reached). */
+int otm_adjoint_result(otm_handle *h, void *adj_ws, double *theta_bar, double *dubar_host);
+
+/* ---------------------------------------------------------------------------------------
  * Stand-alone kernels (device pointers, caller-owned; enqueued on `stream`, not synchronised)
  * ------------------------------------------------------------------------------------- */
 

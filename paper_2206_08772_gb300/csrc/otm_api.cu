@@ -23,6 +23,10 @@ struct otm_handle {
     int64_t step;
     long long launches;
     int64_t n_eroded, n_removed;
+    int64_t nn0, nm0;              // sizes at initialisation (array capacities)
+    // adjoint
+    void *adj_ws;
+    bool adj_swap;
     // phase timing
     bool timing;
     struct Rec {
@@ -109,6 +113,7 @@ static size_t layout(int64_t nn, int64_t nm, int S, int precision, char *base, D
     TAKE(d.rate, double, nm);
     TAKE(d.lam, double, 3 * nm);
     TAKE(d.logz, double, nm);
+    TAKE(d.logz_in, double, nm);
     TAKE(d.mat_id, int32_t, nm);
     TAKE(d.cnt, int32_t, nm);
     TAKE(d.newton_it, int32_t, nm);
@@ -252,6 +257,8 @@ extern "C" int otm_init(const otm_problem *prob, const otm_params *params, void 
     h->ws_bytes = ws_bytes;
     layout(nn, nm, params->max_support, params->precision, (char *)workspace, &h->D, &h->scan_tmp);
     fill_params(h->D, params);
+    h->nn0 = nn;
+    h->nm0 = nm;
     Dev &D = h->D;
     cudaStream_t s = h->stream;
     int rc = OTM_OK;
@@ -528,6 +535,204 @@ extern "C" void otm_destroy(otm_handle *h)
         cudaEventDestroy(r.b);
     }
     delete h;
+}
+
+// ------------------------------------------------------------------ snapshots
+// A snapshot holds everything a step reads except what the LME kernel regenerates bit for bit
+// (shape functions, node-major contributions, ranks, offsets): node and MP state, the support
+// lists, and the exponent shift the last LME solve used.
+struct SnapHeader {
+    int64_t nn, nm, step, magic;
+};
+struct SnapField {
+    void *p;
+    size_t row;
+    int kind;   // 0 node rows, 1 MP rows, 2 padded pair rows
+};
+
+static int snap_fields(otm_handle *h, SnapField *f)
+{
+    Dev &D = h->D;
+    const size_t S = (size_t)D.S;
+    int k = 0;
+    f[k++] = {D.x, 32, 0}; f[k++] = {D.x_prev, 32, 0}; f[k++] = {D.du, 32, 0}; f[k++] = {D.du32, 16, 0};
+    f[k++] = {D.nflags, 1, 0}; f[k++] = {D.ngid, 8, 0};
+    f[k++] = {D.xp, 32, 1}; f[k++] = {D.F, 72, 1}; f[k++] = {D.dF, 72, 1}; f[k++] = {D.be, 48, 1};
+    f[k++] = {D.sig, 48, 1}; f[k++] = {D.vol, 8, 1}; f[k++] = {D.mass, 8, 1}; f[k++] = {D.ebar, 8, 1};
+    f[k++] = {D.T, 8, 1}; f[k++] = {D.rate, 8, 1}; f[k++] = {D.lam, 24, 1}; f[k++] = {D.logz, 8, 1};
+    f[k++] = {D.logz_in, 8, 1}; f[k++] = {D.mat_id, 4, 1}; f[k++] = {D.mgid, 8, 1}; f[k++] = {D.cnt, 4, 1};
+    f[k++] = {D.newton_it, 4, 1}; f[k++] = {D.failed, 1, 1};
+    f[k++] = {D.ids, 4 * S, 1};
+    return k;
+}
+
+static size_t snap_size(otm_handle *h)
+{
+    SnapField f[32];
+    const int n = snap_fields(h, f);
+    size_t b = 256;
+    for (int i = 0; i < n; i++) b += a256(f[i].row * (size_t)(f[i].kind == 0 ? h->nn0 : h->nm0));
+    return b;
+}
+
+extern "C" int otm_snapshot_bytes(otm_handle *h, size_t *bytes)
+{
+    if (!h || !bytes) return OTM_ERR_ARG;
+    *bytes = snap_size(h);
+    return OTM_OK;
+}
+
+extern "C" int otm_snapshot_save(otm_handle *h, void *dst)
+{
+    if (!h || !dst || (((uintptr_t)dst) & 255)) return OTM_ERR_ARG;
+    SnapField f[32];
+    const int n = snap_fields(h, f);
+    SnapHeader hd = {h->D.nn, h->D.nm, h->step, 0x4f544d53};
+    CK(cudaMemcpyAsync(dst, &hd, sizeof(hd), cudaMemcpyHostToDevice, h->stream));
+    char *o = (char *)dst + 256;
+    for (int i = 0; i < n; i++) {
+        const size_t rows = (size_t)(f[i].kind == 0 ? h->D.nn : h->D.nm);
+        CK(cudaMemcpyAsync(o, f[i].p, f[i].row * rows, cudaMemcpyDeviceToDevice, h->stream));
+        o += a256(f[i].row * (size_t)(f[i].kind == 0 ? h->nn0 : h->nm0));
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    return OTM_OK;
+}
+
+extern "C" int otm_snapshot_load(otm_handle *h, const void *src)
+{
+    if (!h || !src || (((uintptr_t)src) & 255)) return OTM_ERR_ARG;
+    SnapHeader hd;
+    CK(cudaMemcpy(&hd, src, sizeof(hd), cudaMemcpyDeviceToHost));
+    if (hd.magic != 0x4f544d53 || hd.nn > h->nn0 || hd.nm > h->nm0) return OTM_ERR_ARG;
+    h->D.nn = hd.nn;
+    h->D.nm = hd.nm;
+    h->step = hd.step;
+    SnapField f[32];
+    const int n = snap_fields(h, f);
+    const char *o = (const char *)src + 256;
+    for (int i = 0; i < n; i++) {
+        const size_t rows = (size_t)(f[i].kind == 0 ? h->D.nn : h->D.nm);
+        CK(cudaMemcpyAsync(f[i].p, o, f[i].row * rows, cudaMemcpyDeviceToDevice, h->stream));
+        o += a256(f[i].row * (size_t)(f[i].kind == 0 ? h->nn0 : h->nm0));
+    }
+    Dev &D = h->D;
+    // regenerate ranks, offsets, shape functions and contributions: the LME restarts from the
+    // stored lambda with the stored exponent shift, so it reproduces them exactly
+    CK(cudaMemsetAsync(D.err, 0xff, sizeof(unsigned long long), h->stream));
+    CK(cudaMemsetAsync(D.ncount, 0, (size_t)D.nn * sizeof(int32_t), h->stream));
+    CK(cudaMemsetAsync(D.emax, 0x80, 2 * sizeof(int), h->stream));
+    CK(launch_rebuild_ranks(D, h->stream, &h->launches));
+    CK(launch_node_offsets(D, h->scan_tmp, h->stream, &h->launches));
+    CK(cudaMemcpyAsync(D.logz, D.logz_in, (size_t)D.nm * 8, cudaMemcpyDeviceToDevice, h->stream));
+    CK(launch_lme(D, h->stream, &h->launches));
+    return read_error(h, nullptr, nullptr);
+}
+
+// ------------------------------------------------------------------ adjoint
+static size_t adj_layout(otm_handle *h, char *base, AdjDev *A)
+{
+    const int64_t nn = h->nn0, nm = h->nm0, slots = nm * (int64_t)h->D.S;
+    size_t off = 256;
+#define ATAKE(ptr, T, count)                                        \
+    do {                                                            \
+        if (base) A->ptr = (T *)(base + off);                       \
+        off += a256((size_t)(count) * sizeof(T));                   \
+    } while (0)
+    ATAKE(xb, double4_32a, nn); ATAKE(dub, double4_32a, nn); ATAKE(rb, double4_32a, nn);
+    ATAKE(Fb, double, 9 * nm); ATAKE(beb, double, 6 * nm); ATAKE(ebb, double, nm); ATAKE(Tb, double, nm);
+    ATAKE(vb, double, nm); ATAKE(sigb, double, 6 * nm); ATAKE(dFb, double, 9 * nm); ATAKE(thb, double, 5 * nm);
+    ATAKE(xpb, double4_32a, nm);
+    ATAKE(pb_cur, double4_32a, slots); ATAKE(pb_prev, double4_32a, slots);
+    ATAKE(du_n, double4_32a, nn);
+    ATAKE(F_n, double, 9 * nm); ATAKE(be_n, double, 6 * nm); ATAKE(ebar_n, double, nm); ATAKE(T_n, double, nm);
+    ATAKE(vol_n, double, nm); ATAKE(sig_n, double, 6 * nm);
+    ATAKE(shape_n, double4_32a, slots); ATAKE(ids_n, int32_t, slots); ATAKE(cnt_n, int32_t, nm);
+    ATAKE(noff_n, int32_t, nn + 1); ATAKE(rank_n, uint16_t, slots);
+    ATAKE(sc1, double4_32a, slots); ATAKE(sc3a, double4_32a, slots); ATAKE(sc3b, double4_32a, slots);
+#undef ATAKE
+    return off;
+}
+
+static AdjDev adj_view(otm_handle *h)
+{
+    AdjDev A;
+    memset(&A, 0, sizeof(A));
+    adj_layout(h, (char *)h->adj_ws, &A);
+    if (h->adj_swap) {
+        double4_32a *t = A.pb_cur;
+        A.pb_cur = A.pb_prev;
+        A.pb_prev = t;
+    }
+    return A;
+}
+
+extern "C" int otm_adjoint_bytes(otm_handle *h, size_t *bytes)
+{
+    if (!h || !bytes) return OTM_ERR_ARG;
+    AdjDev A;
+    *bytes = adj_layout(h, nullptr, &A);
+    return OTM_OK;
+}
+
+extern "C" int otm_adjoint_begin(otm_handle *h, void *adj_ws, size_t bytes, const double *xbar_host)
+{
+    if (!h || !adj_ws || !xbar_host || (((uintptr_t)adj_ws) & 255)) return OTM_ERR_ARG;
+    AdjDev A;
+    const size_t need = adj_layout(h, nullptr, &A);
+    if (bytes < need) return OTM_ERR_WORKSPACE;
+    if (h->P.allow_erode) return OTM_ERR_ARG;   // the adjoint keeps the node and MP sets fixed
+    h->adj_ws = adj_ws;
+    h->adj_swap = false;
+    CK(cudaMemsetAsync(adj_ws, 0, need, h->stream));
+    A = adj_view(h);
+    CK(cudaMemcpy2DAsync(A.xb, 32, xbar_host, 24, 24, (size_t)h->D.nn, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return OTM_OK;
+}
+
+extern "C" int otm_adjoint_step(otm_handle *h, void *adj_ws)
+{
+    if (!h || !adj_ws || adj_ws != h->adj_ws) return OTM_ERR_ARG;
+    AdjDev A = adj_view(h);
+    Dev &D = h->D;
+    cudaStream_t s = h->stream;
+    const size_t nn = (size_t)D.nn, nm = (size_t)D.nm, slots = nm * (size_t)D.S;
+    // copies of state n that the recomputed step overwrites
+    CK(cudaMemcpyAsync(A.du_n, D.du, 32 * nn, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(A.F_n, D.F, 72 * nm, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(A.be_n, D.be, 48 * nm, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(A.ebar_n, D.ebar, 8 * nm, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(A.T_n, D.T, 8 * nm, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(A.vol_n, D.vol, 8 * nm, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(A.sig_n, D.sig, 48 * nm, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(A.shape_n, D.shape, 32 * slots, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(A.ids_n, D.ids, 4 * slots, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(A.cnt_n, D.cnt, 4 * nm, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(A.rank_n, D.rank, 2 * slots, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(A.noff_n, D.noff, 4 * (nn + 1), cudaMemcpyDeviceToDevice, s));
+    // step n again (deterministic: reproduces the trajectory), then back-propagate through it
+    int rc = enqueue_step(h);
+    if (rc != OTM_OK) return rc;
+    CK(launch_adjoint_backward(D, A, s, &h->launches));
+    h->adj_swap = !h->adj_swap;   // the adjoint of shape n becomes the current pair adjoint
+    return read_error(h, nullptr, nullptr);
+}
+
+extern "C" int otm_adjoint_result(otm_handle *h, void *adj_ws, double *theta_bar, double *dubar_host)
+{
+    if (!h || !adj_ws || adj_ws != h->adj_ws || !theta_bar) return OTM_ERR_ARG;
+    AdjDev A = adj_view(h);
+    const size_t nm = (size_t)h->D.nm;
+    std::vector<double> th(5 * nm);
+    CK(cudaMemcpyAsync(th.data(), A.thb, 5 * nm * 8, cudaMemcpyDeviceToHost, h->stream));
+    if (dubar_host)
+        CK(cudaMemcpy2DAsync(dubar_host, 24, A.dub, 32, 24, (size_t)h->D.nn, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    for (int k = 0; k < 5; k++) theta_bar[k] = 0.0;
+    for (size_t p = 0; p < nm; p++)   // fixed order: deterministic
+        for (int k = 0; k < 5; k++) theta_bar[k] += th[5 * p + k];
+    return OTM_OK;
 }
 
 // ------------------------------------------------------------------ stand-alone entries

@@ -57,7 +57,7 @@ struct Dev {
     float4 *spos32;                  // the same relative to the grid origin in FP32, w = ID bits
     // material points
     double4_32a *xp;
-    double *F, *dF, *be, *sig, *vol, *mass, *ebar, *T, *rate, *lam, *logz;
+    double *F, *dF, *be, *sig, *vol, *mass, *ebar, *T, *rate, *lam, *logz, *logz_in;
     int32_t *mat_id, *cnt, *newton_it;
     uint8_t *failed;
     int64_t *mgid;
@@ -81,6 +81,24 @@ struct SearchScratch {
     unsigned long long *err;
     int max_cells;
 };
+
+// adjoint state and the copies of state n used by one backward step (otm_adjoint.cu)
+struct AdjDev {
+    // adjoint state (of state n+1 on entry, of state n on exit)
+    double4_32a *xb, *dub, *rb;        // nodes; rb = (dL/dr_I, dL/dm_I)
+    double *Fb, *beb, *ebb, *Tb, *vb, *sigb, *dFb, *thb;   // MPs (thb: 5 per MP, accumulated)
+    double4_32a *xpb;
+    double4_32a *pb_cur, *pb_prev;     // pairs: (dL/dN, dL/dgradN) of shape n+1 / shape n
+    // copies of state n taken before the step is recomputed
+    double4_32a *du_n;
+    double *F_n, *be_n, *ebar_n, *T_n, *vol_n, *sig_n;
+    double4_32a *shape_n;
+    int32_t *ids_n, *cnt_n, *noff_n;
+    uint16_t *rank_n;
+    // per-pair node contributions in node-major order
+    double4_32a *sc1, *sc3a, *sc3b;
+};
+
 
 // ---------------------------------------------------------------------------------------
 __device__ __forceinline__ void raise_error(unsigned long long *err, int code, long long id)
@@ -229,6 +247,8 @@ bool carve_search_scratch(void *base, size_t bytes, int64_t nn, SearchScratch *S
 cudaError_t build_search_grid(const double *node_x, int64_t nn, double cell, SearchScratch *S,
                               double *grid_out, cudaStream_t s);
 size_t lme_smem_bytes(int S, int warps);
+cudaError_t launch_adjoint_backward(const Dev &D, const AdjDev &A, cudaStream_t s, long long *launches);
+cudaError_t launch_rebuild_ranks(const Dev &D, cudaStream_t s, long long *launches);
 cudaError_t erode_mps(Dev &D, int32_t *scan_tmp, int64_t *n_drop_host, cudaStream_t s, long long *launches);
 cudaError_t remove_orphan_nodes(Dev &D, int32_t *scan_tmp, int64_t *n_drop_host, cudaStream_t s,
                                 long long *launches);

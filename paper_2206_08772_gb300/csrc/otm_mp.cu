@@ -12,6 +12,7 @@
 //                  linear hardening closed form, Johnson-Cook safeguarded Newton), heating,
 //                  fracture flag, sigma = tau / J
 #include "otm_dev.cuh"
+#include "otm_rm.cuh"
 
 namespace otm {
 
@@ -386,6 +387,7 @@ __global__ void __launch_bounds__(kLmeWarps * kWarp) k_lme(const Dev D)
         D.newton_it[p] = iters;
         if (st == OTM_OK) {
             D.lam[3 * p] = l0; D.lam[3 * p + 1] = l1; D.lam[3 * p + 2] = l2;
+            D.logz_in[p] = D.logz[p];
             D.logz[p] = E.shift + log(E.Z);
         } else {
             raise_error(D.err, st, D.mgid[p]);
@@ -514,172 +516,6 @@ cudaError_t launch_kinematics(const Dev &D, cudaStream_t s, long long *launches)
         k_kinematics<false><<<blocks, 128, 0, s>>>(D);
     if (launches) *launches += 1;
     return cudaGetLastError();
-}
-
-// ======================================================================== return map
-// cyclic Jacobi (Golub & Van Loan Sec. 8.5) on a symmetric 3x3, rotations applied in place
-__device__ void jacobi_sym3(double A[3][3], double V[3][3])
-{
-    for (int i = 0; i < 3; i++)
-        for (int j = 0; j < 3; j++) V[i][j] = (i == j) ? 1.0 : 0.0;
-    double nrm = 0.0;
-    for (int i = 0; i < 3; i++)
-        for (int j = 0; j < 3; j++) nrm += A[i][j] * A[i][j];
-    nrm = sqrt(nrm);
-    for (int sweep = 0; sweep < 60; sweep++) {
-        double off = sqrt(2.0 * (A[0][1] * A[0][1] + A[0][2] * A[0][2] + A[1][2] * A[1][2]));
-        if (off <= 1e-15 * nrm) break;
-        for (int r = 0; r < 3; r++) {
-            const int p = (r == 2) ? 1 : 0, q = (r == 0) ? 1 : 2;
-            const double apq = A[p][q];
-            if (apq == 0.0) continue;
-            const double app = A[p][p], aqq = A[q][q];
-            const double th = (aqq - app) / (2.0 * apq);
-            const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-            const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
-            const int k = 3 - p - q;
-            const double akp = A[k][p], akq = A[k][q];
-            A[k][p] = A[p][k] = c * akp - s * akq;
-            A[k][q] = A[q][k] = s * akp + c * akq;
-            A[p][p] = c * c * app - 2.0 * c * s * apq + s * s * aqq;
-            A[q][q] = s * s * app + 2.0 * c * s * apq + c * c * aqq;
-            A[p][q] = A[q][p] = 0.0;
-            for (int i = 0; i < 3; i++) {
-                const double vp = V[i][p], vq = V[i][q];
-                V[i][p] = c * vp - s * vq;
-                V[i][q] = s * vp + c * vq;
-            }
-        }
-    }
-}
-
-__device__ __forceinline__ void jc_sigma_y(const otm_material &M, double ebar_n, double x, double dt,
-                                           double T, double &sy, double &dsy)
-{
-    const double ebar = ebar_n + x;
-    const double tstar = fmin(fmax((T - M.T_room) / (M.T_melt - M.T_room), 0.0), 1.0);
-    const double therm = 1.0 - pow(tstar, M.m);
-    const double rstar = (x / dt) / M.eps_dot0;
-    double rate = 1.0, drate = 0.0;
-    if (rstar > 1.0) {
-        rate = 1.0 + M.C * log(rstar);
-        drate = M.C / x;
-    }
-    const double hard = M.A + M.B * pow(ebar, M.n);
-    const double dhard = (ebar > 0.0) ? M.B * M.n * pow(ebar, M.n - 1.0) : INFINITY;
-    sy = hard * rate * therm;
-    dsy = (dhard * rate + hard * drate) * therm;
-}
-
-struct RmIn {
-    double dF[9], be[6], ebar, T, J;
-};
-struct RmOut {
-    double sig[6], be[6], ebar, T, rate;
-    bool failed;
-};
-
-// returns OTM_OK or an error code
-__device__ int return_map_point(const otm_material &M, double dt, const RmIn &in, RmOut &out)
-{
-    const double K = M.E / (3.0 * (1.0 - 2.0 * M.nu));
-    const double mu = M.E / (2.0 * (1.0 + M.nu));
-    // trial b = dF b_n dF^T
-    const double b[3][3] = {{in.be[0], in.be[3], in.be[5]}, {in.be[3], in.be[1], in.be[4]},
-                            {in.be[5], in.be[4], in.be[2]}};
-    double t[3][3];
-    for (int i = 0; i < 3; i++)
-        for (int j = 0; j < 3; j++)
-            t[i][j] = in.dF[3 * i] * b[0][j] + in.dF[3 * i + 1] * b[1][j] + in.dF[3 * i + 2] * b[2][j];
-    double A[3][3];
-    for (int i = 0; i < 3; i++)
-        for (int j = 0; j < 3; j++)
-            A[i][j] = t[i][0] * in.dF[3 * j] + t[i][1] * in.dF[3 * j + 1] + t[i][2] * in.dF[3 * j + 2];
-    for (int i = 0; i < 3; i++)
-        for (int j = i + 1; j < 3; j++) A[i][j] = A[j][i] = 0.5 * (A[i][j] + A[j][i]);
-    double Q[3][3];
-    jacobi_sym3(A, Q);
-    double e[3];
-    for (int a = 0; a < 3; a++) {
-        if (!(A[a][a] > 0.0)) return OTM_ERR_JACOBIAN;
-        e[a] = 0.5 * log(A[a][a]);
-    }
-    const double tr = e[0] + e[1] + e[2];
-    double s[3], sn2 = 0.0;
-    for (int a = 0; a < 3; a++) {
-        s[a] = 2.0 * mu * (e[a] - tr / 3.0);
-        sn2 += s[a] * s[a];
-    }
-    const double sn = sqrt(sn2);
-    const double q_tr = 1.2247448713915890491 * sn;   // sqrt(3/2) |s|
-    double dep = 0.0;
-    if (M.model == 0) {
-        const double f_tr = sn - 0.81649658092772603273 * (M.sigma_y0 + M.H * in.ebar);
-        if (f_tr > 0.0) dep = 0.81649658092772603273 * f_tr / (2.0 * mu + 2.0 * M.H / 3.0);
-    } else {
-        double sy0, dsy0;
-        jc_sigma_y(M, in.ebar, 0.0, dt, in.T, sy0, dsy0);
-        if (q_tr - sy0 > 0.0) {
-            double lo = 0.0, hi = q_tr / (3.0 * mu), x = 0.5 * hi;
-            const double tol = 1e-12 * q_tr;
-            bool ok = false;
-            for (int it = 0; it < 300; it++) {
-                double sy, dsy;
-                jc_sigma_y(M, in.ebar, x, dt, in.T, sy, dsy);
-                const double g = q_tr - 3.0 * mu * x - sy;
-                if (fabs(g) <= tol) { ok = true; break; }
-                if (g > 0.0) lo = x; else hi = x;
-                if (hi - lo <= 4e-16 * hi) { ok = true; break; }
-                double xn = x - g / (-3.0 * mu - dsy);
-                if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
-                x = xn;
-            }
-            if (!ok) return OTM_ERR_RETURNMAP_NOCONV;
-            dep = x;
-        }
-    }
-    const double dgamma = 1.2247448713915890491 * dep;
-    const double qn = q_tr - 3.0 * mu * dep;
-    double tau[3], eb2[3];
-    for (int a = 0; a < 3; a++) {
-        const double na = (sn > 0.0) ? s[a] / sn : 0.0;
-        e[a] -= dgamma * na;
-        tau[a] = K * tr + 2.0 * mu * (e[a] - tr / 3.0);
-        eb2[a] = exp(2.0 * e[a]);
-    }
-    const double iJ = 1.0 / in.J;
-    const int I[6] = {0, 1, 2, 0, 1, 0}, Jx[6] = {0, 1, 2, 1, 2, 2};
-    for (int c = 0; c < 6; c++) {
-        const int i = I[c], j = Jx[c];
-        double vb = 0.0, vs = 0.0;
-        for (int a = 0; a < 3; a++) {
-            const double qq = Q[i][a] * Q[j][a];
-            vb += eb2[a] * qq;
-            vs += tau[a] * qq;
-        }
-        out.be[c] = vb;
-        out.sig[c] = vs * iJ;
-    }
-    out.ebar = in.ebar + dep;
-    out.rate = dep / dt;
-    out.T = in.T;
-    if (M.model == 1 && M.chi > 0.0 && dep > 0.0) out.T = in.T + M.chi * qn * dep / (M.rho0 * M.cp);
-    out.failed = false;
-    if (M.model == 1 && M.fracture && out.ebar > 0.0) {
-        const double pr = K * tr * iJ;
-        const double sv = fmax(qn, 0.0) * iJ;
-        // triaxiality; its limit sign(p) * inf where no deviatoric stress is left (melted point)
-        const double eta = (sv > 1e-12 * fabs(pr)) ? pr / sv : (pr > 0.0 ? INFINITY : (pr < 0.0 ? -INFINITY : 0.0));
-        const double texp = (M.d3 == 0.0) ? 1.0 : exp(M.d3 * eta);
-        const double rstar = out.rate / M.eps_dot0;
-        const double lr = (rstar > 1.0) ? log(rstar) : 0.0;
-        const double tstar = fmin(fmax((out.T - M.T_room) / (M.T_melt - M.T_room), 0.0), 1.0);
-        const double ef = (M.d1 + M.d2 * texp) * (1.0 + M.d4 * lr) * (1.0 + M.d5 * tstar);
-        out.failed = (out.ebar >= ef);
-    }
-    for (int c = 0; c < 6; c++)
-        if (!isfinite(out.sig[c])) return OTM_ERR_NONFINITE;
-    return OTM_OK;
 }
 
 __global__ void __launch_bounds__(128) k_return_map(const Dev D)

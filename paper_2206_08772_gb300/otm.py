@@ -138,6 +138,40 @@ class OTM:
         check(_lib.load().otm_phase_times(self._h, ms, n), "otm_phase_times")
         return {k: (ms[i], n[i]) for i, k in enumerate(_lib.PHASES)}
 
+    # -- snapshots and the adjoint (device buffers are torch uint8 tensors, 256-byte aligned)
+    def _aligned(self, nbytes):
+        t = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        return t, (t.data_ptr() + 255) & ~255
+
+    def snapshot(self):
+        L = _lib.load()
+        nb = C.c_size_t(0)
+        check(L.otm_snapshot_bytes(self._h, C.byref(nb)), "otm_snapshot_bytes")
+        buf, ptr = self._aligned(nb.value)
+        check(L.otm_snapshot_save(self._h, C.c_void_p(ptr)), "otm_snapshot_save")
+        return (buf, ptr)
+
+    def restore(self, snap):
+        check(_lib.load().otm_snapshot_load(self._h, C.c_void_p(snap[1])), "otm_snapshot_load")
+
+    def adjoint_begin(self, xbar: np.ndarray):
+        L = _lib.load()
+        nb = C.c_size_t(0)
+        check(L.otm_adjoint_bytes(self._h, C.byref(nb)), "otm_adjoint_bytes")
+        self._adj_buf, self._adj_ptr = self._aligned(nb.value)
+        xb = np.ascontiguousarray(xbar, dtype=np.float64)
+        check(L.otm_adjoint_begin(self._h, C.c_void_p(self._adj_ptr), nb.value, _ptr(xb)), "otm_adjoint_begin")
+
+    def adjoint_step(self):
+        check(_lib.load().otm_adjoint_step(self._h, C.c_void_p(self._adj_ptr)), "otm_adjoint_step")
+
+    def adjoint_result(self):
+        thb = np.zeros(5)
+        dub = np.zeros((self.counts()["n_nodes"], 3))
+        check(_lib.load().otm_adjoint_result(self._h, C.c_void_p(self._adj_ptr), _ptr(thb), _ptr(dub)),
+              "otm_adjoint_result")
+        return thb, dub
+
     def refresh(self) -> int:
         return _lib.load().otm_refresh(self._h)
 
