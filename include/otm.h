@@ -135,6 +135,11 @@ int otm_counts(otm_handle *h, int64_t *n_nodes, int64_t *n_mps, int64_t *n_pairs
 /* Copy one field to host memory (bytes must equal the field size). Synchronises the stream. */
 int otm_state(otm_handle *h, int32_t field, void *host_dst, size_t bytes);
 
+/* Copy selected rows of a per-MP or per-node field (rows: host array of n_rows indices; bytes
+ * = n_rows x the field's row size). SUPPORT_IDS / SHAPE rows are ordered by node ID. Synchronises. */
+int otm_state_rows(otm_handle *h, int32_t field, const int64_t *rows, int64_t n_rows, void *host_dst,
+                   size_t bytes);
+
 /* Overwrite one field from host memory (NODE_X, NODE_DU, MP_X, F, BE, SIGMA, VOL, EBAR, T,
  * LAMBDA). Supports and shape functions are rebuilt by otm_refresh. */
 int otm_set_state(otm_handle *h, int32_t field, const void *host_src, size_t bytes);

@@ -78,6 +78,7 @@ _SIGS = {
     "otm_counts": (C.c_int, [_P, _P, _P, _P, _P]),
     "otm_state": (C.c_int, [_P, _I32, _P, _SZ]),
     "otm_set_state": (C.c_int, [_P, _I32, _P, _SZ]),
+    "otm_state_rows": (C.c_int, [_P, _I32, _P, _I64, _P, _SZ]),
     "otm_refresh": (C.c_int, [_P]),
     "otm_error_detail": (C.c_int, [_P, _P, _P]),
     "otm_kernel_launches": (C.c_int, [_P, _P]),

@@ -464,6 +464,43 @@ extern "C" int otm_state(otm_handle *h, int32_t field, void *host_dst, size_t by
     return OTM_OK;
 }
 
+extern "C" int otm_state_rows(otm_handle *h, int32_t field, const int64_t *rows, int64_t n_rows, void *host_dst,
+                              size_t bytes)
+{
+    if (!h || !rows || !host_dst || n_rows < 0) return OTM_ERR_ARG;
+    FieldView v;
+    if (!field_view(h, field, &v)) return OTM_ERR_ARG;
+    if (bytes != v.width * (size_t)n_rows) return OTM_ERR_ARG;
+    for (int64_t r = 0; r < n_rows; r++) {
+        if (rows[r] < 0 || (size_t)rows[r] >= v.rows) return OTM_ERR_ARG;
+        CK(cudaMemcpyAsync((char *)host_dst + (size_t)r * v.width, (const char *)v.src + (size_t)rows[r] * v.pitch,
+                           v.width, cudaMemcpyDeviceToHost, h->stream));
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    if (field == OTM_FIELD_SUPPORT_IDS || field == OTM_FIELD_SHAPE) {   // order each row by node ID
+        const size_t S = (size_t)h->D.S;
+        std::vector<int32_t> cnt(n_rows), ids(S);
+        for (int64_t r = 0; r < n_rows; r++) {
+            CK(cudaMemcpy(&cnt[r], h->D.cnt + rows[r], sizeof(int32_t), cudaMemcpyDeviceToHost));
+            const int n = cnt[r];
+            if (field == OTM_FIELD_SUPPORT_IDS) {
+                int32_t *row = (int32_t *)host_dst + (size_t)r * S;
+                std::sort(row, row + n);
+            } else {
+                CK(cudaMemcpy(ids.data(), h->D.ids + (size_t)rows[r] * S, S * sizeof(int32_t), cudaMemcpyDeviceToHost));
+                std::vector<int> perm(n);
+                std::iota(perm.begin(), perm.end(), 0);
+                std::sort(perm.begin(), perm.end(), [&](int a, int b) { return ids[a] < ids[b]; });
+                double *sh = (double *)host_dst + (size_t)r * S * 4;
+                std::vector<double> tmp(sh, sh + 4 * (size_t)n);
+                for (int k = 0; k < n; k++)
+                    for (int c = 0; c < 4; c++) sh[4 * k + c] = tmp[4 * perm[k] + c];
+            }
+        }
+    }
+    return OTM_OK;
+}
+
 extern "C" int otm_set_state(otm_handle *h, int32_t field, const void *host_src, size_t bytes)
 {
     if (!h || !host_src) return OTM_ERR_ARG;

@@ -193,6 +193,20 @@ class OTM:
         del c
         return out
 
+    def get_rows(self, name: str, rows) -> np.ndarray:
+        """Selected rows of a per-MP (or per-node) field; support rows ordered by node ID."""
+        r = np.ascontiguousarray(rows, dtype=np.int64)
+        if name == "support_ids":
+            out = np.empty((r.size, self.S), np.int32)
+        elif name == "shape":
+            out = np.empty((r.size, self.S, 4), np.float64)
+        else:
+            w, dt = _WIDTH[name]
+            out = np.empty((r.size, w) if w > 1 else (r.size,), dt)
+        check(_lib.load().otm_state_rows(self._h, FIELD[name], _ptr(r), r.size, _ptr(out), out.nbytes),
+              f"otm_state_rows({name})")
+        return out
+
     def n_current(self):
         c = self.counts()
         return c["n_nodes"], c["n_mps"]
