@@ -7,6 +7,7 @@ LME shape functions, node-major lists). Metric: material-point-steps/s = n_mps *
 
 value       : FP64 path, inputs resident in HBM, CUDA events on the library's stream.
 mixed       : the FP32-scatter / FP64-Newton path on the same workload.
+adjoint     : adjoint/forward time ratio of the hand-written GPU adjoint on the 202,752-MP rod.
 e2e         : the same metric through the C ABI with pinned host buffers: otm_init (H2D of the
               problem + initial supports) + every step followed by a D2H of the node positions.
 roofline    : the dominant kernel of the step (largest phase time) against its ALU peak.
@@ -49,6 +50,17 @@ SEARCH_PER_CAND, CAND_PER_PAIR = 8, 3.73
 KIN_PER_PAIR = 24
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 2 FP64 FMA lanes / SM / clock at 2070 MHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def aggregate(ms_local: float, n_mps: int, steps: int, world: int, dist, device="cpu"):
+    """Replicas: every rank runs its own rod; the job time is the slowest rank's (max over ranks)
+    and the value counts the material-point steps of all ranks."""
+    import torch
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    return ms, world * n_mps * steps / (ms / 1e3)
 
 
 def workload(name: str, seed: int = 0):
@@ -206,6 +218,40 @@ def time_e2e(prob, precision, steps, torch):
                 d2h_bytes_per_step=int(out.nbytes), seconds=t)
 
 
+def time_adjoint(steps: int, torch):
+    """Adjoint/forward time ratio on the 202,752-MP Johnson-Cook rod (h 0.29 mm): forward of
+    `steps` steps with ceil(sqrt(steps)) checkpoints, then the backward pass (segment recompute +
+    backward steps) for one objective."""
+    import math
+
+    from paper_2206_08772_gb300.adjoint import backward_pass, objectives_and_seeds
+    from paper_2206_08772_gb300.otm import OTM
+    prob = workload("taylor_jc_h0.29")
+    every = int(math.ceil(math.sqrt(steps)))
+    sim = OTM(prob, precision="fp64")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    checkpoints = {0: sim.snapshot()}
+    for k in range(steps):
+        if sim.step(1) != 0:
+            raise RuntimeError("adjoint forward failed")
+        if (k + 1) % every == 0 and k + 1 < steps:
+            checkpoints[k + 1] = sim.snapshot()
+    final = sim.snapshot()
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - t0
+    vals, seeds, _ = objectives_and_seeds(sim.get("node_x"), sim.get("node_mass"), prob.h)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    grad = backward_pass(sim, prob, steps, every, checkpoints, final, seeds[0])
+    torch.cuda.synchronize()
+    t_bwd = time.perf_counter() - t0
+    sim.close()
+    return {"workload": "taylor_jc_h0.29 (38,181 nodes, 202,752 MPs), JC copper", "steps": steps,
+            "checkpoint_every": every, "forward_s": t_fwd, "backward_s": t_bwd, "ratio": t_bwd / t_fwd,
+            "objective": "final length", "dL_dtheta": dict(zip(("A", "B", "n", "C", "m", "v0"), grad.tolist()))}
+
+
 def time_oracle(prob, steps: int, warmup: int = 0):
     import oracle
     samp = cpu_sample(prob)
@@ -235,6 +281,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adjoint-steps", type=int, default=46)
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -276,21 +324,23 @@ def main():
     sim.close()
     del sim
     torch.cuda.empty_cache()
-    ms_t = torch.tensor([info["ms"]], device="cuda")
-    if dist is not None:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms = float(ms_t.item())
-    value = world * prob.n_mps * args.steps / (ms / 1e3)
+    ms, value = aggregate(info["ms"], prob.n_mps, args.steps, world, dist, device="cuda")
 
     mixed = None
     if not args.no_mixed:
         simm, infom = time_gpu(prob, "mixed", args.steps, args.warmup, torch, dist)
+        phases_m = phase_profile(simm)
         simm.close()
         del simm
         torch.cuda.empty_cache()
         mv = world * prob.n_mps * args.steps / (infom["ms"] / 1e3)
         mixed = {"value": mv, "unit": UNIT, "ms_per_step": infom["ms"] / args.steps,
-                 "speedup_vs_fp64": mv / value, "dtype": "f32 scatter/node update, f64 elsewhere"}
+                 "speedup_vs_fp64": mv / value, "dtype": "f32 scatter/node update, f64 elsewhere",
+                 "phases_ms": phases_m}
+    adjoint = None
+    if not args.no_adjoint and rank == 0:
+        adjoint = time_adjoint(args.adjoint_steps, torch)
+        torch.cuda.empty_cache()
     e2e = None
     if not args.no_e2e:
         e2e = time_e2e(prob, "fp64", args.steps, torch)
@@ -328,6 +378,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
             "gpu_launches": info["launches"], "mixed": mixed, "e2e": e2e, "roofline": roofline,
+            "adjoint": adjoint,
             "cpu_baseline": cpu, "clocks": clk.summary(),
             "stats": {"mean_support": n_bar, "mean_newton_iterations": k_bar},
             "phases_ms": phases}

@@ -148,3 +148,35 @@ def test_chip_tool_contact_erosion_compaction(orc, OTM, embed_h, steps):
     if embed_h >= 3.0:
         assert eroded > 100
         assert sim_o.counts()["n_nodes"] < p.n_nodes
+
+
+def test_sweep_mixed_vs_fp64_final_geometry(orc, OTM):
+    """Sweep of small rods of uneven size (h, v0 and the JC constants A, B varied from a seed):
+    final length and footprint radius of the FP64 and mixed GPU paths against the FP64 oracle."""
+    import math
+    rng = np.random.default_rng(5)
+    rows = []
+    for k, h in enumerate((0.6e-3, 0.7e-3, 0.8e-3)):
+        v0 = rng.uniform(150, 300)
+        A, B = 90e6 * rng.uniform(0.9, 1.1), 292e6 * rng.uniform(0.9, 1.1)
+        p = scenarios.taylor_rod(h=h, R=3.2e-3, L=6.4e-3, v0=v0, material=scenarios.copper_jc(A=A, B=B))
+        steps = 25
+        so = orc.Sim(p)
+        assert so.step(steps) == 0
+        xo = so.get("node_x")
+        act = so.get("node_mass") > 0
+        Lo = xo[act, 2].max()
+        foot = xo[:, 2] <= 1e-3 * p.h
+        Ro = np.hypot(xo[foot, 0], xo[foot, 1]).max()
+        errs = {}
+        for prec in ("fp64", "mixed"):
+            g = OTM(p, precision=prec)
+            assert g.step(steps) == 0
+            x = g.get("node_x")
+            Lg = x[act, 2].max()
+            Rg = np.hypot(x[foot, 0], x[foot, 1]).max()
+            errs[prec] = (abs(Lg - Lo) / Lo, abs(Rg - Ro) / Ro)
+        rows.append((h, v0, errs))
+        assert max(errs["fp64"]) <= 1e-12
+        assert max(errs["mixed"]) <= 1e-7
+    print("sweep", rows)
