@@ -23,8 +23,8 @@ namespace otm {
 // with n = 64 m + j = round(64 x / ln 2) from the 1.5*2^52 shifter, r by a two-term split of
 // ln2/64 (the high part has 36 significant bits, so n * L1 is exact for |n| < 2^17), and
 // exp(r) - 1 by its Taylor polynomial of degree 5 (truncation below 4e-17 relative). The table
-// 2^(j/64) is filled per block from exp2(). Valid for -700 <= x <= 700; below -700 it returns 0
-// (a weight below 1e-304 of the largest), above 700 +inf (the caller then re-shifts).
+// 2^(j/64) is filled per block from exp2(). Valid for x in about [-707, 708]; below it returns 0 (a
+// weight below 1e-307 of the largest), above +inf (the caller then re-shifts).
 constexpr double kExpInvL = 0x1.71547652b82fep+6;    // 64 / ln 2
 constexpr double kExpL1 = 0x1.62e42fefa0000p-7;      // ln 2 / 64, high part
 constexpr double kExpL2 = 0x1.cf79abc9e3b3ap-46;     // ln 2 / 64 - kExpL1
@@ -38,10 +38,13 @@ __device__ __forceinline__ void exp_table_fill(double *T)
 
 __device__ __forceinline__ double exp_tang(double x, const double *T)
 {
-    if (x < -700.0) return 0.0;
-    if (!(x <= 700.0)) return x > 700.0 ? INFINITY : x;   // +inf for large x, NaN passes through
     const double t = fma(x, kExpInvL, kExpShifter);
     const int n = __double2loint(t);
+    // range by an integer test on n = round(64 x / ln 2): the result 2^m T_j p stays a normal
+    // double for m = n >> 6 in [-1020, 1021] (x in about [-707, 708]); inputs are finite here
+    // (non-finite positions stop the step before the LME kernel runs)
+    if (n < -65280) return 0.0;
+    if (n > 65400) return INFINITY;
     const double nd = t - kExpShifter;
     double r = fma(-nd, kExpL1, x);
     r = fma(-nd, kExpL2, r);
@@ -62,17 +65,15 @@ struct LmeSums {
     double shift;
 };
 
-__device__ __forceinline__ void lme_sums(const double *dx, const double *dy, const double *dz, const double *q,
-                                         double *w, int n, double l0, double l1, double l2, double shift,
-                                         int lane, const double *T, LmeSums &E)
+template <bool SHIFTED>
+__device__ __forceinline__ void lme_accumulate(const double *dx, const double *dy, const double *dz, const double *q,
+                                               double *w, int n, double l0, double l1, double l2, double qs,
+                                               int lane, const double *T, double (&v)[16])
 {
-    double v[16];
-#pragma unroll
-    for (int i = 0; i < 16; i++) v[i] = 0.0;
-    const double qs = -shift;
     for (int k = lane; k < n; k += kWarp) {
         const double x = dx[k], y = dy[k], z = dz[k];
-        const double f = fma(l2, z, fma(l1, y, fma(l0, x, q[k] + qs)));
+        const double qk = SHIFTED ? q[k] + qs : q[k];
+        const double f = fma(l2, z, fma(l1, y, fma(l0, x, qk)));
         const double wk = exp_tang(f, T);
         w[k] = wk;
         const double wx = wk * x, wy = wk * y, wz = wk * z;
@@ -81,6 +82,22 @@ __device__ __forceinline__ void lme_sums(const double *dx, const double *dy, con
         v[4] = fma(wx, x, v[4]); v[5] = fma(wy, y, v[5]); v[6] = fma(wz, z, v[6]);
         v[7] = fma(wx, y, v[7]); v[8] = fma(wy, z, v[8]); v[9] = fma(wx, z, v[9]);
     }
+}
+
+__device__ __forceinline__ void lme_sums(const double *dx, const double *dy, const double *dz, const double *q,
+                                         double *w, int n, double l0, double l1, double l2, double shift,
+                                         double q0shift, int lane, const double *T, LmeSums &E)
+{
+    double v[16];
+#pragma unroll
+    for (int i = 0; i < 16; i++) v[i] = 0.0;
+    // q[] holds the prior exponent minus the solve's first shift; a different shift (only after
+    // an over/underflow) is applied as a difference
+    const double qs = q0shift - shift;
+    if (qs == 0.0)
+        lme_accumulate<false>(dx, dy, dz, q, w, n, l0, l1, l2, qs, lane, T, v);
+    else
+        lme_accumulate<true>(dx, dy, dz, q, w, n, l0, l1, l2, qs, lane, T, v);
     const double t = warp_reduce_scatter16(v, lane);   // value j at lanes 2j, 2j+1
     E.Z = __shfl_sync(0xffffffffu, t, 0);
     E.r0 = __shfl_sync(0xffffffffu, t, 2);
@@ -97,22 +114,23 @@ __device__ __forceinline__ void lme_sums(const double *dx, const double *dy, con
 
 __device__ __forceinline__ double lme_fmax(const double *dx, const double *dy, const double *dz,
                                            const double *q, int n, double l0, double l1, double l2,
-                                           int lane)
+                                           double q0shift, int lane)
 {
     double m = -INFINITY;
     for (int k = lane; k < n; k += kWarp) m = fmax(m, q[k] + (l0 * dx[k] + l1 * dy[k] + l2 * dz[k]));
-    return warp_max(m);
+    return warp_max(m) + q0shift;
 }
 
 // evaluation with the given shift; if the weights over- or underflow, again with max f
 __device__ __forceinline__ void lme_sums_safe(const double *dx, const double *dy, const double *dz,
                                               const double *q, double *w, int n, double l0, double l1,
-                                              double l2, double shift, int lane, const double *T, LmeSums &E)
+                                              double l2, double shift, double q0shift, int lane, const double *T,
+                                              LmeSums &E)
 {
-    lme_sums(dx, dy, dz, q, w, n, l0, l1, l2, shift, lane, T, E);
+    lme_sums(dx, dy, dz, q, w, n, l0, l1, l2, shift, q0shift, lane, T, E);
     if (!(E.Z > 1e-200) || !(E.Z < 1e200)) {
-        const double fm = lme_fmax(dx, dy, dz, q, n, l0, l1, l2, lane);
-        lme_sums(dx, dy, dz, q, w, n, l0, l1, l2, fm, lane, T, E);
+        const double fm = lme_fmax(dx, dy, dz, q, n, l0, l1, l2, q0shift, lane);
+        lme_sums(dx, dy, dz, q, w, n, l0, l1, l2, fm, q0shift, lane, T, E);
     }
 }
 
@@ -149,15 +167,14 @@ __device__ __forceinline__ bool logz_less(const LmeSums &t, const LmeSums &c)
 // Damped Newton on the convex log Z(lambda): step -J^-1 (r/Z) = -J'^-1 r, halved until log Z or
 // the residual norm drops; stops when |r| / Z <= tol. All evaluations of one solve share the
 // initial shift (the previous step's log Z, so w ~ N), which makes the log Z comparison a
-// comparison of Z. On return w[] holds the weights of the accepted evaluation E. Warp-uniform.
-__device__ int lme_newton(const double *dx, const double *dy, const double *dz, const double *q, double *w,
-                          int n, double &l0, double &l1, double &l2, double shift, double tol, int max_it,
-                          int lane, const double *T, LmeSums &E, int &iters)
+// comparison of Z; q[] must hold the prior exponent minus that shift. On return w[] holds the
+// weights of the accepted evaluation E. Warp-uniform.
+// Newton iterations from an evaluation E already taken at lambda (see lme_newton).
+__device__ int lme_newton_loop(const double *dx, const double *dy, const double *dz, const double *q, double *w,
+                               int n, double &l0, double &l1, double &l2, double shift, double tol, int max_it,
+                               int lane, const double *T, LmeSums &E, int &iters)
 {
-    iters = 0;
-    if (n <= 0) return OTM_ERR_LME_NOCONV;
     const double tol2 = tol * tol;
-    lme_sums_safe(dx, dy, dz, q, w, n, l0, l1, l2, shift, lane, T, E);
     for (;;) {
         const double r2 = rn2(E);
         if (!isfinite(r2) || !isfinite(E.Z)) return OTM_ERR_LME_NOCONV;
@@ -175,7 +192,7 @@ __device__ int lme_newton(const double *dx, const double *dy, const double *dz, 
         double m0 = l0, m1 = l1, m2 = l2;
         for (int halving = 0; halving < 40; halving++) {
             m0 = fma(t, s0, l0); m1 = fma(t, s1, l1); m2 = fma(t, s2, l2);
-            lme_sums_safe(dx, dy, dz, q, w, n, m0, m1, m2, E.shift, lane, T, Et);
+            lme_sums_safe(dx, dy, dz, q, w, n, m0, m1, m2, E.shift, shift, lane, T, Et);
             if (isfinite(Et.Z) && (logz_less(Et, E) || rn2(Et) * (E.Z * E.Z) < r2 * (Et.Z * Et.Z))) {
                 accepted = true;
                 break;
@@ -186,6 +203,21 @@ __device__ int lme_newton(const double *dx, const double *dy, const double *dz, 
         l0 = m0; l1 = m1; l2 = m2;
         E = Et;
     }
+}
+
+// Damped Newton on the convex log Z(lambda): step -J^-1 (r/Z) = -J'^-1 r, halved until log Z or
+// the residual norm drops; stops when |r| / Z <= tol. All evaluations of one solve share the
+// initial shift (the previous step's log Z, so w ~ N), which makes the log Z comparison a
+// comparison of Z; q[] must hold the prior exponent minus that shift. On return w[] holds the
+// weights of the accepted evaluation E. Warp-uniform.
+__device__ int lme_newton(const double *dx, const double *dy, const double *dz, const double *q, double *w,
+                          int n, double &l0, double &l1, double &l2, double shift, double tol, int max_it,
+                          int lane, const double *T, LmeSums &E, int &iters)
+{
+    iters = 0;
+    if (n <= 0) return OTM_ERR_LME_NOCONV;
+    lme_sums_safe(dx, dy, dz, q, w, n, l0, l1, l2, shift, shift, lane, T, E);
+    return lme_newton_loop(dx, dy, dz, q, w, n, l0, l1, l2, shift, tol, max_it, lane, T, E, iters);
 }
 
 // ======================================================================== support search
@@ -300,7 +332,18 @@ __device__ __forceinline__ WarpSmem warp_smem(unsigned char *base, int S, int wa
 
 constexpr int kLmeWarps = 4;
 
-size_t lme_smem_bytes(int S, int warps) { return 64 * sizeof(double) + (size_t)warps * 5 * (size_t)S * sizeof(double); }
+// per block: the exp table, the per-warp pair arrays, and the batched first-evaluation records
+struct FirstEval {
+    double sums[11];   // Z, r(3), A(6), shift
+    double inv[6], iZ, logz;
+    int ok;            // 1: converged at the first evaluation, 0: Newton iterations needed
+    int pad;
+};
+
+size_t lme_smem_bytes(int S, int warps)
+{
+    return 64 * sizeof(double) + (size_t)warps * 5 * (size_t)S * sizeof(double) + (size_t)warps * sizeof(FirstEval);
+}
 
 size_t search_lme_smem_bytes(int S, int warps) { return lme_smem_bytes(S, warps); }
 
@@ -357,51 +400,100 @@ __global__ void __launch_bounds__(kLmeWarps * kWarp) k_lme(const Dev D)
     exp_table_fill(T);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t p = (int64_t)blockIdx.x * kLmeWarps + warp;
-    if (p >= D.nm) return;
-    if (has_error(D.err)) return;
     const int S = D.S;
+    FirstEval *FE = (FirstEval *)(smem_raw + 64 * sizeof(double) + (size_t)kLmeWarps * 5 * (size_t)S * sizeof(double));
+    // every warp reaches the two block barriers below; idle warps skip the work
+    const bool active = (p < D.nm) && !has_error(D.err);
     WarpSmem W = warp_smem(smem_raw + 64 * sizeof(double), S, warp);
-    const double4_32a xp = D.xp[p];
-    const int cnt = D.cnt[p];
     const int64_t base = p * (int64_t)S;
-
-    // d_a = x_p - x_a and the prior exponent -beta |d_a|^2
-    const double beta = D.beta;
-    for (int k = lane; k < cnt; k += kWarp) {
-        const double4_32a a = D.x[D.ids[base + k]];
-        const double x = xp.x - a.x, y = xp.y - a.y, z = xp.z - a.z;
-        W.dx[k] = x; W.dy[k] = y; W.dz[k] = z;
-        W.q[k] = -beta * fma(z, z, fma(y, y, x * x));
-    }
-    __syncwarp();
-
-    // Eq. 14: Newton for lambda, warm-started from the previous step
-    double l0 = D.lam[3 * p], l1 = D.lam[3 * p + 1], l2 = D.lam[3 * p + 2];
+    int cnt = 0;
+    double4_32a xp = make_double4_32a(0, 0, 0, 0);
+    double l0 = 0, l1 = 0, l2 = 0, shift0 = 0;
     LmeSums E;
+    if (active) {
+        xp = D.xp[p];
+        cnt = D.cnt[p];
+        // d_a = x_p - x_a and the prior exponent -beta |d_a|^2, minus the Newton solve's shift
+        const double beta = D.beta;
+        shift0 = D.logz[p];
+        for (int k = lane; k < cnt; k += kWarp) {
+            const double4_32a a = D.x[D.ids[base + k]];
+            const double x = xp.x - a.x, y = xp.y - a.y, z = xp.z - a.z;
+            W.dx[k] = x; W.dy[k] = y; W.dz[k] = z;
+            W.q[k] = fma(-beta, fma(z, z, fma(y, y, x * x)), -shift0);
+        }
+        __syncwarp();
+        // Eq. 14: the first evaluation at the previous step's lambda (warm start)
+        l0 = D.lam[3 * p]; l1 = D.lam[3 * p + 1]; l2 = D.lam[3 * p + 2];
+        if (cnt > 0) lme_sums_safe(W.dx, W.dy, W.dz, W.q, W.w, cnt, l0, l1, l2, shift0, shift0, lane, T, E);
+        if (lane == 0) {
+            const double s11[11] = {E.Z, E.r0, E.r1, E.r2, E.a00, E.a11, E.a22, E.a01, E.a12, E.a02, E.shift};
+            for (int i = 0; i < 11; i++) FE[warp].sums[i] = (cnt > 0) ? s11[i] : 0.0;
+        }
+    }
+    __syncthreads();
+    // the convergence test, J'^-1, 1/Z and log Z of the block's MPs, one lane per MP
+    if (warp == 0 && lane < kLmeWarps) {
+        const int64_t q = (int64_t)blockIdx.x * kLmeWarps + lane;
+        FirstEval &f = FE[lane];
+        f.ok = 0;
+        if (q < D.nm) {
+            LmeSums e;
+            e.Z = f.sums[0]; e.r0 = f.sums[1]; e.r1 = f.sums[2]; e.r2 = f.sums[3];
+            e.a00 = f.sums[4]; e.a11 = f.sums[5]; e.a22 = f.sums[6]; e.a01 = f.sums[7]; e.a12 = f.sums[8];
+            e.a02 = f.sums[9]; e.shift = f.sums[10];
+            const double r2 = rn2(e);
+            const double tol = D.tol_abs;
+            if (e.Z > 0.0 && isfinite(r2) && isfinite(e.Z) && r2 <= tol * tol * e.Z * e.Z && lme_jinv(e, f.inv)) {
+                f.ok = 1;
+                f.iZ = 1.0 / e.Z;
+                f.logz = e.shift + log(e.Z);
+            }
+        }
+    }
+    __syncthreads();
+    if (!active) return;
+    double inv[6], iZ;
     int iters = 0;
-    int st = lme_newton(W.dx, W.dy, W.dz, W.q, W.w, cnt, l0, l1, l2, D.logz[p], D.tol_abs, D.max_newton, lane, T,
-                        E, iters);
-    double inv[6];
-    if (st == OTM_OK && !lme_jinv(E, inv)) st = OTM_ERR_LME_NOCONV;
-    if (lane == 0) {
-        D.newton_it[p] = iters;
-        if (st == OTM_OK) {
-            D.lam[3 * p] = l0; D.lam[3 * p + 1] = l1; D.lam[3 * p + 2] = l2;
-            D.logz_in[p] = D.logz[p];
-            D.logz[p] = E.shift + log(E.Z);
-        } else {
-            raise_error(D.err, st, D.mgid[p]);
+    int st = OTM_OK;
+    if (FE[warp].ok) {
+        for (int i = 0; i < 6; i++) inv[i] = FE[warp].inv[i];
+        iZ = FE[warp].iZ;
+        if (lane == 0) {
+            D.newton_it[p] = 0;
+            D.logz_in[p] = shift0;
+            D.logz[p] = FE[warp].logz;
+        }
+    } else {
+        // Newton iterations (rare with the warm start): per warp, from the first evaluation
+        if (cnt <= 0) st = OTM_ERR_LME_NOCONV;
+        else st = lme_newton_loop(W.dx, W.dy, W.dz, W.q, W.w, cnt, l0, l1, l2, shift0, D.tol_abs, D.max_newton,
+                                  lane, T, E, iters);
+        if (st == OTM_OK && !lme_jinv(E, inv)) st = OTM_ERR_LME_NOCONV;
+        iZ = 1.0 / E.Z;
+        if (lane == 0) {
+            D.newton_it[p] = iters;
+            if (st == OTM_OK) {
+                D.lam[3 * p] = l0; D.lam[3 * p + 1] = l1; D.lam[3 * p + 2] = l2;
+                D.logz_in[p] = shift0;
+                D.logz[p] = E.shift + log(E.Z);
+            } else {
+                raise_error(D.err, st, D.mgid[p]);
+            }
         }
     }
     if (st != OTM_OK) return;
 
     // N_a = w_a / Z, grad N_a = -N_a J^-1 d_a = -w_a J'^-1 d_a; contributions for Eq. 5 of the next
     // step, stored at the pair's place in its node's influence list
-    const double iZ = 1.0 / E.Z;
     const double mp = D.mass[p], vp = D.vol[p];
     const double *sg = D.sig + 6 * p;
-    const double sxx = sg[0], syy = sg[1], szz = sg[2], sxy = sg[3], syz = sg[4], sxz = sg[5];
+    // -v_p sigma_p, so that the force contribution is one 3x3 product with grad N
+    const double sxx = -vp * sg[0], syy = -vp * sg[1], szz = -vp * sg[2], sxy = -vp * sg[3], syz = -vp * sg[4],
+                 sxz = -vp * sg[5];
     int em = -2000, ef = -2000;   // largest binary exponents of the stored mass / force terms
+    const float fsxx = (float)sxx, fsyy = (float)syy, fszz = (float)szz, fsxy = (float)sxy, fsyz = (float)syz,
+                fsxz = (float)sxz;
     for (int k = lane; k < cnt; k += kWarp) {
         const double wk = W.w[k];
         const double N = wk * iZ;
@@ -414,19 +506,18 @@ __global__ void __launch_bounds__(kLmeWarps * kWarp) k_lme(const Dev D)
         const int64_t pos = (int64_t)D.noff[id] + D.rank[base + k];
         if (MIXED) {
             const float fgx = (float)gx, fgy = (float)gy, fgz = (float)gz;
-            const float fv = (float)vp;
             const float c0 = (float)(mp * N);
-            const float c1 = -fv * fmaf((float)sxz, fgz, fmaf((float)sxy, fgy, (float)sxx * fgx));
-            const float c2 = -fv * fmaf((float)syz, fgz, fmaf((float)syy, fgy, (float)sxy * fgx));
-            const float c3 = -fv * fmaf((float)szz, fgz, fmaf((float)syz, fgy, (float)sxz * fgx));
+            const float c1 = fmaf(fsxz, fgz, fmaf(fsxy, fgy, fsxx * fgx));
+            const float c2 = fmaf(fsyz, fgz, fmaf(fsyy, fgy, fsxy * fgx));
+            const float c3 = fmaf(fszz, fgz, fmaf(fsyz, fgy, fsxz * fgx));
             D.contrib32[pos] = make_float4(c0, c1, c2, c3);
             em = max(em, fexp32(c0));
             ef = max(ef, max(fexp32(c1), max(fexp32(c2), fexp32(c3))));
         } else {
             const double cm = mp * N;
-            const double fx = -vp * (sxx * gx + sxy * gy + sxz * gz);
-            const double fy = -vp * (sxy * gx + syy * gy + syz * gz);
-            const double fz = -vp * (sxz * gx + syz * gy + szz * gz);
+            const double fx = sxx * gx + sxy * gy + sxz * gz;
+            const double fy = sxy * gx + syy * gy + syz * gz;
+            const double fz = sxz * gx + syz * gy + szz * gz;
             D.contrib64[pos] = make_double4_32a(cm, fx, fy, fz);
             em = max(em, fexp64(cm));
             ef = max(ef, max(fexp64(fx), max(fexp64(fy), fexp64(fz))));
@@ -480,14 +571,10 @@ __global__ void __launch_bounds__(128) k_kinematics(const Dev D)
         const int id = D.ids[base + k];
         const double4_32a sh = D.shape[base + k];
         const double4_32a xa = D.x[id];
-        double u0, u1, u2;
-        if (MIXED) {
-            const float4 u = D.du32[id];
-            u0 = u.x; u1 = u.y; u2 = u.z;
-        } else {
-            const double4_32a u = D.du[id];
-            u0 = u.x; u1 = u.y; u2 = u.z;
-        }
+        // the node kernel stores every increment in FP64 as well (in the mixed path it is the
+        // FP32 increment, widened), so both paths read the FP64 copy
+        const double4_32a u = D.du[id];
+        const double u0 = u.x, u1 = u.y, u2 = u.z;
         v[0] = fma(sh.x, xa.x, v[0]); v[1] = fma(sh.x, xa.y, v[1]); v[2] = fma(sh.x, xa.z, v[2]);
         v[3] = fma(u0, sh.y, v[3]); v[4] = fma(u0, sh.z, v[4]); v[5] = fma(u0, sh.w, v[5]);
         v[6] = fma(u1, sh.y, v[6]); v[7] = fma(u1, sh.z, v[7]); v[8] = fma(u1, sh.w, v[8]);
@@ -648,7 +735,9 @@ __global__ void __launch_bounds__(kLmeWarps * kWarp)
     }
     __syncwarp();
     double l0 = lam[3 * p], l1 = lam[3 * p + 1], l2 = lam[3 * p + 2];
-    const double shift = lme_fmax(W.dx, W.dy, W.dz, W.q, n, l0, l1, l2, lane);
+    const double shift = lme_fmax(W.dx, W.dy, W.dz, W.q, n, l0, l1, l2, 0.0, lane);
+    for (int k = lane; k < n; k += kWarp) W.q[k] -= shift;
+    __syncwarp();
     LmeSums E;
     int iters = 0;
     int st = lme_newton(W.dx, W.dy, W.dz, W.q, W.w, n, l0, l1, l2, shift, tol, max_newton, lane, T, E, iters);
