@@ -355,9 +355,12 @@ def main():
     work = {   # kernel -> (algorithmic TFLOP per launch, peak, bound)
         "lme": (pairs * (LME_PER_PAIR_SETUP + LME_PER_PAIR_EVAL * (1 + k_bar) + LME_PER_PAIR_FINAL) / 1e12,
                 FP64_PEAK_TFLOPS, "fp64"),
-        "search": (pairs * CAND_PER_PAIR * SEARCH_PER_CAND / 1e12, FP32_PEAK_TFLOPS, "fp32"),
-        "kinematics": (pairs * KIN_PER_PAIR / 1e12, FP64_PEAK_TFLOPS, "fp64"),
     }
+    if phases.get("kinematics", 0.0) > 0.0:     # separate kernels
+        work["search"] = (pairs * CAND_PER_PAIR * SEARCH_PER_CAND / 1e12, FP32_PEAK_TFLOPS, "fp32")
+        work["kinematics"] = (pairs * KIN_PER_PAIR / 1e12, FP64_PEAK_TFLOPS, "fp64")
+    else:                                        # fused kinematics + search: its FP64 part
+        work["search"] = (pairs * KIN_PER_PAIR / 1e12, FP64_PEAK_TFLOPS, "fp64")
     kernels = {}
     for k, (tf, peak, kind) in work.items():
         ms_k = phases[k]

@@ -307,7 +307,35 @@ static int enqueue_step(otm_handle *h)
         PhaseScope ps(h, OTM_PHASE_NODE_UPDATE);
         CK(launch_node_update(D, t_next, s, &h->launches));
     }
-    {   // 3: MP position, F, volume
+    if (!D.allow_erode) {
+        // no MP can leave the body within the step: the kinematics gather (3) and the search at
+        // the new MP position (5) run in one kernel, then the return map (4) and the LME (6)
+        {
+            PhaseScope ps(h, OTM_PHASE_GRID);
+            CK(launch_grid_build(D, s, &h->launches));
+        }
+        CK(cudaMemsetAsync(D.ncount, 0, (size_t)D.nn * sizeof(int32_t), s));
+        CK(cudaMemsetAsync(D.emax, 0x80, 2 * sizeof(int), s));
+        {
+            PhaseScope ps(h, OTM_PHASE_SEARCH);
+            CK(launch_kin_search(D, s, &h->launches));
+        }
+        {
+            PhaseScope ps(h, OTM_PHASE_NODE_MAJOR);
+            CK(launch_node_offsets(D, h->scan_tmp, s, &h->launches));
+        }
+        {
+            PhaseScope ps(h, OTM_PHASE_RETURN_MAP);
+            CK(launch_return_map(D, s, &h->launches));
+        }
+        {
+            PhaseScope ps(h, OTM_PHASE_LME);
+            CK(launch_lme(D, s, &h->launches));
+        }
+        h->step++;
+        return OTM_OK;
+    }
+    {   // 3: MP position, F increment
         PhaseScope ps(h, OTM_PHASE_KINEMATICS);
         CK(launch_kinematics(D, s, &h->launches));
     }
@@ -316,7 +344,7 @@ static int enqueue_step(otm_handle *h)
         CK(launch_return_map(D, s, &h->launches));
     }
     int64_t eroded = 0;
-    if (D.allow_erode) {   // fracture: failed MPs leave before the new supports are built
+    {   // fracture: failed MPs leave before the new supports are built
         PhaseScope ps(h, OTM_PHASE_COMPACT);
         CK(erode_mps(D, h->scan_tmp, &eroded, s, &h->launches));
         h->n_eroded += eroded;

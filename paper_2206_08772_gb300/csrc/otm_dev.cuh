@@ -231,6 +231,7 @@ __host__ __device__ __forceinline__ int next_pow2(int v)
 // Each returns cudaGetLastError() of its launches; `launches` counts kernels enqueued.
 cudaError_t launch_grid_build(const Dev &D, cudaStream_t s, long long *launches);
 cudaError_t launch_search(const Dev &D, cudaStream_t s, long long *launches);
+cudaError_t launch_kin_search(const Dev &D, cudaStream_t s, long long *launches);
 cudaError_t launch_lme(const Dev &D, cudaStream_t s, long long *launches);
 cudaError_t launch_node_offsets(const Dev &D, int32_t *tmp, cudaStream_t s, long long *launches);
 cudaError_t launch_exp_selftest(const double *x, int64_t n, double *mine, double *ref, cudaStream_t s);

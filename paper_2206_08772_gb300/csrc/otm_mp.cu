@@ -381,6 +381,78 @@ __global__ void __launch_bounds__(kSearchWarps * kWarp) k_search(const Dev D)
     if (lane == 0) D.cnt[p] = cnt;
 }
 
+// ======================================================================== k_kin_search
+// Kinematics (Eq. 9, 11) and the support search at the new position (Algorithm 3) in one warp
+// per MP: the gather over the old support gives x_p and dF, then the candidate scan builds the
+// new support in the same row. Used when no erosion can remove MPs between the two; the
+// return map (which only needs dF) follows.
+__global__ void __launch_bounds__(kSearchWarps * kWarp) k_kin_search(const Dev D)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t p = (int64_t)blockIdx.x * kSearchWarps + warp;
+    if (p >= D.nm) return;
+    if (has_error(D.err)) return;
+    const int S = D.S;
+    const int n = D.cnt[p];
+    const int64_t base = p * (int64_t)S;
+    double v[16];
+#pragma unroll
+    for (int i = 0; i < 16; i++) v[i] = 0.0;
+    for (int k = lane; k < n; k += kWarp) {
+        const int id = D.ids[base + k];
+        const double4_32a sh = D.shape[base + k];
+        const double4_32a xa = D.x[id];
+        const double4_32a u = D.du[id];
+        v[0] = fma(sh.x, xa.x, v[0]); v[1] = fma(sh.x, xa.y, v[1]); v[2] = fma(sh.x, xa.z, v[2]);
+        v[3] = fma(u.x, sh.y, v[3]); v[4] = fma(u.x, sh.z, v[4]); v[5] = fma(u.x, sh.w, v[5]);
+        v[6] = fma(u.y, sh.y, v[6]); v[7] = fma(u.y, sh.z, v[7]); v[8] = fma(u.y, sh.w, v[8]);
+        v[9] = fma(u.z, sh.y, v[9]); v[10] = fma(u.z, sh.z, v[10]); v[11] = fma(u.z, sh.w, v[11]);
+    }
+    const double t = warp_reduce_scatter16(v, lane);
+    const int j = lane >> 1;
+    if ((lane & 1) == 0 && j >= 3 && j < 12) {
+        const int c = j - 3;
+        D.dF[9 * p + c] = (c == 0 || c == 4 || c == 8) ? 1.0 + t : t;
+    }
+    const double px = __shfl_sync(0xffffffffu, t, 0), py = __shfl_sync(0xffffffffu, t, 2),
+                 pz = __shfl_sync(0xffffffffu, t, 4);
+    if (lane == 0) {
+        D.xp[p] = make_double4_32a(px, py, pz, 0.0);
+        if (!isfinite(px) || !isfinite(py) || !isfinite(pz)) raise_error(D.err, OTM_ERR_NONFINITE, D.mgid[p]);
+    }
+    __syncwarp();   // the old row is read completely before the new support overwrites it
+    int32_t *list = (int32_t *)smem_raw + (size_t)warp * next_pow2(S);
+    SearchGrid G{D.grid, D.cell_start, D.spos32, D.spos};
+    const int cnt = warp_support_search(G, D.cell, D.rs2, px, py, pz, list, S, lane);
+    if (cnt > S) {
+        if (lane == 0) {
+            raise_error(D.err, OTM_ERR_CAPACITY, D.mgid[p]);
+            D.cnt[p] = 0;
+        }
+        return;
+    }
+    __syncwarp();
+    for (int k = lane; k < cnt; k += kWarp) {
+        const int id = list[k];
+        D.ids[base + k] = id;
+        const int r = atomicAdd(&D.ncount[id], 1);
+        if (r > 0xffff) raise_error(D.err, OTM_ERR_CAPACITY, D.ngid[id]);
+        D.rank[base + k] = (uint16_t)r;
+    }
+    if (lane == 0) D.cnt[p] = cnt;
+}
+
+cudaError_t launch_kin_search(const Dev &D, cudaStream_t s, long long *launches)
+{
+    const size_t smem = (size_t)kSearchWarps * next_pow2(D.S) * sizeof(int32_t);
+    const unsigned blocks = (unsigned)((D.nm + kSearchWarps - 1) / kSearchWarps);
+    if (blocks == 0) return cudaSuccess;
+    k_kin_search<<<blocks, kSearchWarps * kWarp, smem, s>>>(D);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_search(const Dev &D, cudaStream_t s, long long *launches)
 {
     const size_t smem = (size_t)kSearchWarps * next_pow2(D.S) * sizeof(int32_t);
