@@ -102,6 +102,7 @@ static size_t layout(int64_t nn, int64_t nm, int S, int precision, char *base, D
     TAKE(tmp, int32_t, scan_tmp_ints((nn > nm ? nn : nm) + 1));
     // material points
     TAKE(d.xp, double4_32a, nm);
+    TAKE(d.xp_prev, double4_32a, nm);
     TAKE(d.F, double, 9 * nm);
     TAKE(d.dF, double, 9 * nm);
     TAKE(d.be, double, 6 * nm);
@@ -151,7 +152,7 @@ static int check_params(int64_t nn, int64_t nm, const otm_params *P)
     if (!(P->cell_size * 2.0 >= sqrt(P->rs2))) return OTM_ERR_ARG;   // stencil of +-2 cells
     if (nm * (int64_t)P->max_support >= (int64_t)0x7fffffff) return OTM_ERR_ARG;
     if (nn >= (int64_t)0x7fffffff / 16) return OTM_ERR_ARG;
-    if (P->eps_stab != 0.0) return OTM_ERR_ARG;   // stabilisation term: not in the CUDA path
+    if (!(P->eps_stab >= 0.0)) return OTM_ERR_ARG;
     return OTM_OK;
 }
 
@@ -622,7 +623,7 @@ static int snap_fields(otm_handle *h, SnapField *f)
     int k = 0;
     f[k++] = {D.x, 32, 0}; f[k++] = {D.x_prev, 32, 0}; f[k++] = {D.du, 32, 0}; f[k++] = {D.du32, 16, 0};
     f[k++] = {D.nflags, 1, 0}; f[k++] = {D.ngid, 8, 0};
-    f[k++] = {D.xp, 32, 1}; f[k++] = {D.F, 72, 1}; f[k++] = {D.dF, 72, 1}; f[k++] = {D.be, 48, 1};
+    f[k++] = {D.xp, 32, 1}; f[k++] = {D.xp_prev, 32, 1}; f[k++] = {D.F, 72, 1}; f[k++] = {D.dF, 72, 1}; f[k++] = {D.be, 48, 1};
     f[k++] = {D.sig, 48, 1}; f[k++] = {D.vol, 8, 1}; f[k++] = {D.mass, 8, 1}; f[k++] = {D.ebar, 8, 1};
     f[k++] = {D.T, 8, 1}; f[k++] = {D.rate, 8, 1}; f[k++] = {D.lam, 24, 1}; f[k++] = {D.logz, 8, 1};
     f[k++] = {D.logz_in, 8, 1}; f[k++] = {D.mat_id, 4, 1}; f[k++] = {D.mgid, 8, 1}; f[k++] = {D.cnt, 4, 1};
@@ -747,6 +748,7 @@ extern "C" int otm_adjoint_begin(otm_handle *h, void *adj_ws, size_t bytes, cons
     const size_t need = adj_layout(h, nullptr, &A);
     if (bytes < need) return OTM_ERR_WORKSPACE;
     if (h->P.allow_erode) return OTM_ERR_ARG;   // the adjoint keeps the node and MP sets fixed
+    if (h->P.eps_stab != 0.0) return OTM_ERR_ARG;   // the stabilisation term is not differentiated
     h->adj_ws = adj_ws;
     h->adj_swap = false;
     CK(cudaMemsetAsync(adj_ws, 0, need, h->stream));

@@ -56,7 +56,7 @@ struct Dev {
     double4_32a *spos;               // node positions in (cell, ID) order, w = ID bits
     float4 *spos32;                  // the same relative to the grid origin in FP32, w = ID bits
     // material points
-    double4_32a *xp;
+    double4_32a *xp, *xp_prev;       // position and the position of the previous step
     double *F, *dF, *be, *sig, *vol, *mass, *ebar, *T, *rate, *lam, *logz, *logz_in;
     int32_t *mat_id, *cnt, *newton_it;
     uint8_t *failed;

@@ -418,6 +418,7 @@ __global__ void __launch_bounds__(kSearchWarps * kWarp) k_kin_search(const Dev D
     const double px = __shfl_sync(0xffffffffu, t, 0), py = __shfl_sync(0xffffffffu, t, 2),
                  pz = __shfl_sync(0xffffffffu, t, 4);
     if (lane == 0) {
+        D.xp_prev[p] = D.xp[p];
         D.xp[p] = make_double4_32a(px, py, pz, 0.0);
         if (!isfinite(px) || !isfinite(py) || !isfinite(pz)) raise_error(D.err, OTM_ERR_NONFINITE, D.mgid[p]);
     }
@@ -464,7 +465,7 @@ cudaError_t launch_search(const Dev &D, cudaStream_t s, long long *launches)
 }
 
 // ======================================================================== k_lme
-template <bool MIXED>
+template <bool MIXED, bool STAB>
 __global__ void __launch_bounds__(kLmeWarps * kWarp) k_lme(const Dev D)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -566,6 +567,16 @@ __global__ void __launch_bounds__(kLmeWarps * kWarp) k_lme(const Dev D)
     int em = -2000, ef = -2000;   // largest binary exponents of the stored mass / force terms
     const float fsxx = (float)sxx, fsyy = (float)syy, fszz = (float)szz, fsxy = (float)sxy, fsyz = (float)syz,
                 fsxz = (float)sxz;
+    // stabilisation (Eq. 7-8): -eps N_a e_a / |x_a,n-1 - x_p,n-1|,
+    // e_a = x_a - x_p - dF (x_a,n-1 - x_p,n-1), with dF the increment that led to this state
+    double xq0 = 0, xq1 = 0, xq2 = 0, F00 = 0, F01 = 0, F02 = 0, F10 = 0, F11 = 0, F12 = 0, F20 = 0, F21 = 0, F22 = 0;
+    if (STAB) {
+        const double4_32a q = D.xp_prev[p];
+        xq0 = q.x; xq1 = q.y; xq2 = q.z;
+        const double *Fd = D.dF + 9 * p;
+        F00 = Fd[0]; F01 = Fd[1]; F02 = Fd[2]; F10 = Fd[3]; F11 = Fd[4]; F12 = Fd[5]; F20 = Fd[6]; F21 = Fd[7];
+        F22 = Fd[8];
+    }
     for (int k = lane; k < cnt; k += kWarp) {
         const double wk = W.w[k];
         const double N = wk * iZ;
@@ -576,20 +587,42 @@ __global__ void __launch_bounds__(kLmeWarps * kWarp) k_lme(const Dev D)
         D.shape[base + k] = make_double4_32a(N, gx, gy, gz);
         const int id = D.ids[base + k];
         const int64_t pos = (int64_t)D.noff[id] + D.rank[base + k];
+        double sx = 0.0, sy = 0.0, sz = 0.0;
+        if (STAB) {
+            const double4_32a a = D.x_prev[id];
+            const double q0 = a.x - xq0, q1 = a.y - xq1, q2 = a.z - xq2;
+            const double len = sqrt(q0 * q0 + q1 * q1 + q2 * q2);
+            if (len > 1e-12 * D.h) {
+                const double c = -D.eps_stab * N / len;
+                sx = c * (-x - (F00 * q0 + F01 * q1 + F02 * q2));
+                sy = c * (-y - (F10 * q0 + F11 * q1 + F12 * q2));
+                sz = c * (-z - (F20 * q0 + F21 * q1 + F22 * q2));
+            }
+        }
         if (MIXED) {
             const float fgx = (float)gx, fgy = (float)gy, fgz = (float)gz;
             const float c0 = (float)(mp * N);
-            const float c1 = fmaf(fsxz, fgz, fmaf(fsxy, fgy, fsxx * fgx));
-            const float c2 = fmaf(fsyz, fgz, fmaf(fsyy, fgy, fsxy * fgx));
-            const float c3 = fmaf(fszz, fgz, fmaf(fsyz, fgy, fsxz * fgx));
+            float c1 = fmaf(fsxz, fgz, fmaf(fsxy, fgy, fsxx * fgx));
+            float c2 = fmaf(fsyz, fgz, fmaf(fsyy, fgy, fsxy * fgx));
+            float c3 = fmaf(fszz, fgz, fmaf(fsyz, fgy, fsxz * fgx));
+            if (STAB) {
+                c1 += (float)sx;
+                c2 += (float)sy;
+                c3 += (float)sz;
+            }
             D.contrib32[pos] = make_float4(c0, c1, c2, c3);
             em = max(em, fexp32(c0));
             ef = max(ef, max(fexp32(c1), max(fexp32(c2), fexp32(c3))));
         } else {
             const double cm = mp * N;
-            const double fx = sxx * gx + sxy * gy + sxz * gz;
-            const double fy = sxy * gx + syy * gy + syz * gz;
-            const double fz = sxz * gx + syz * gy + szz * gz;
+            double fx = sxx * gx + sxy * gy + sxz * gz;
+            double fy = sxy * gx + syy * gy + syz * gz;
+            double fz = sxz * gx + syz * gy + szz * gz;
+            if (STAB) {
+                fx += sx;
+                fy += sy;
+                fz += sz;
+            }
             D.contrib64[pos] = make_double4_32a(cm, fx, fy, fz);
             em = max(em, fexp64(cm));
             ef = max(ef, max(fexp64(fx), max(fexp64(fy), fexp64(fz))));
@@ -603,23 +636,25 @@ __global__ void __launch_bounds__(kLmeWarps * kWarp) k_lme(const Dev D)
     }
 }
 
+template <bool MIXED, bool STAB>
+static cudaError_t launch_lme_t(const Dev &D, cudaStream_t s, size_t smem, unsigned blocks)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_lme<MIXED, STAB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_lme<MIXED, STAB><<<blocks, kLmeWarps * kWarp, smem, s>>>(D);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_lme(const Dev &D, cudaStream_t s, long long *launches)
 {
     const size_t smem = lme_smem_bytes(D.S, kLmeWarps);
     const unsigned blocks = (unsigned)((D.nm + kLmeWarps - 1) / kLmeWarps);
     if (blocks == 0) return cudaSuccess;
-    cudaError_t e;
-    if (D.precision == OTM_PRECISION_MIXED) {
-        e = cudaFuncSetAttribute(k_lme<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_lme<true><<<blocks, kLmeWarps * kWarp, smem, s>>>(D);
-    } else {
-        e = cudaFuncSetAttribute(k_lme<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_lme<false><<<blocks, kLmeWarps * kWarp, smem, s>>>(D);
-    }
+    const bool mixed = D.precision == OTM_PRECISION_MIXED, stab = D.eps_stab > 0.0;
+    cudaError_t e = mixed ? (stab ? launch_lme_t<true, true>(D, s, smem, blocks) : launch_lme_t<true, false>(D, s, smem, blocks))
+                          : (stab ? launch_lme_t<false, true>(D, s, smem, blocks) : launch_lme_t<false, false>(D, s, smem, blocks));
     if (launches) *launches += 1;
-    return cudaGetLastError();
+    return e;
 }
 
 // (N, grad N) of every slot of a padded row set, for state export: already stored in shape[]
@@ -656,6 +691,7 @@ __global__ void __launch_bounds__(128) k_kinematics(const Dev D)
     const int j = lane >> 1;
     if ((lane & 1) == 0 && j < 12) {
         if (j < 3) {
+            ((double *)&D.xp_prev[p])[j] = ((const double *)&D.xp[p])[j];
             ((double *)&D.xp[p])[j] = t;
             if (!isfinite(t)) raise_error(D.err, OTM_ERR_NONFINITE, D.mgid[p]);
         } else {

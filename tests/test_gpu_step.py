@@ -180,3 +180,24 @@ def test_sweep_mixed_vs_fp64_final_geometry(orc, OTM):
         assert max(errs["fp64"]) <= 1e-12
         assert max(errs["mixed"]) <= 1e-7
     print("sweep", rows)
+
+
+def test_stabilised_residual_matches_oracle(orc, OTM):
+    """Eq. 7-8: the residual with the under-integration penalty, eps = 1e-3 E h^2."""
+    p = scenarios.taylor_rod(h=0.8e-3, R=3.2e-3, L=6.4e-3, material=scenarios.copper_jc())
+    p.eps_stab = 1e-3 * p.materials[0].E * p.h ** 2
+    sim_o = orc.Sim(p)
+    for prec, tol in (("fp64", 1e-10), ("mixed", 1e-4)):
+        sim_g = OTM(p, precision=prec)
+        if prec == "fp64":
+            assert sim_o.step(20) == 0
+        assert sim_g.step(20) == 0, sim_g.error()
+        errs, bad = compare(sim_g, sim_o, {"default": tol, "node_x": tol * 1e-3 if prec == "mixed" else tol,
+                                           "mp_x": tol * 1e-3 if prec == "mixed" else tol})
+        print("stab", prec, errs)
+        assert not bad, bad
+    # the term changes the trajectory: compare with the unstabilised run
+    q = scenarios.taylor_rod(h=0.8e-3, R=3.2e-3, L=6.4e-3, material=scenarios.copper_jc())
+    plain = orc.Sim(q)
+    assert plain.step(20) == 0
+    assert np.abs(plain.get("node_x") - sim_o.get("node_x")).max() > 1e-9
