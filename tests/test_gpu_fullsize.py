@@ -111,3 +111,139 @@ def test_fullsize_node_mass_and_force(orc, run):
             force -= st1["vol"][q] * (Sm @ dN[k])
         assert abs(m[i] - mass) <= 1e-10 * mass
         assert np.abs(f[i] - force).max() <= 1e-10 * np.abs(f).max()
+
+
+def chip_full(embed_h):
+    h = 1.0e-3 / 68
+    return scenarios.chip_block(h=h, embed=embed_h * h, steps=2)
+
+
+def test_fullsize_chip_mixed_with_erosion(orc):
+    """Chip block at full size (4 x 1 x 0.4 mm, h = 1/68 mm: 527,436 nodes, 2,996,352 MPs), mixed
+    path, tool embedded 1.5 h. Before step 1 the plastic strain of a chosen set of MPs (5000 at
+    rest far from the tool, and every MP within 6 h of the corner (0, L_y, 0)) is raised to 1:
+    at rest the Johnson-Cook fracture strain is (d1 + d2)(1 + 0)(1 + 0) = 0.16, so exactly that
+    set is eroded in step 1, and the corner nodes left with no MP within r_s are removed.
+    Checked: the surviving MP and node IDs (bit-exact, orphans by brute force over the corner);
+    then, through step 2 (support IDs renumbered by the compaction), sampled survivors re-derived
+    by the oracle from the GPU's own state: kinematics, return map, supports (bit-exact), LME."""
+    from paper_2206_08772_gb300.otm import OTM
+    p = chip_full(1.5)
+    h, Lx, Ly = p.h, p.meta["size"][0], p.meta["size"][1]
+    sim = OTM(p, precision="mixed", max_support=384)
+    rng = np.random.default_rng(1)
+    far = np.nonzero(p.mp_x[:, 0] < 0.5 * Lx)[0]
+    corner = np.array([0.0, Ly, 0.0])
+    in_corner = np.nonzero(np.linalg.norm(p.mp_x - corner, axis=1) <= 6 * h)[0]
+    E = np.union1d(rng.choice(far, 5000, replace=False), in_corner)
+    ebar = np.zeros(p.n_mps)
+    ebar[E] = 1.0
+    sim.set("ebar", ebar)
+    assert sim.step(1) == 0, sim.error()
+    gid1 = sim.get("mp_gid")
+    assert np.array_equal(gid1, np.setdiff1d(np.arange(p.n_mps), E))
+    mp1 = sim.get("mp_x")
+    # orphans: nodes near the corner with no surviving MP within r_s (the search's distance test)
+    cand = np.nonzero(np.linalg.norm(p.node_x - corner, axis=1) <= 10 * h)[0]
+    near = np.nonzero(np.linalg.norm(mp1 - corner, axis=1) <= 16 * h)[0]
+    x1 = sim.get("node_x")
+    ngid1 = sim.get("node_gid")
+    orphan = [i for i in cand if brute_support(mp1[near], p.node_x[i], p.rs2).size == 0]
+    assert len(orphan) > 0
+    assert np.array_equal(ngid1, np.setdiff1d(np.arange(p.n_nodes), orphan))
+    st1 = {k: sim.get(k) for k in ("be", "ebar", "T")}
+    near_tool = np.nonzero(mp1[:, 0] > p.contact.tool_x0 - 0.1e-3)[0]
+    by_corner = np.nonzero(np.linalg.norm(mp1 - corner, axis=1) <= 9 * h)[0]
+    rows1 = np.unique(np.concatenate([rng.choice(near_tool, 16, replace=False),
+                                      rng.choice(by_corner, 8, replace=False),
+                                      rng.choice(gid1.size, 8, replace=False)]))
+    ids1 = sim.get_rows("support_ids", rows1)
+    shape1 = sim.get_rows("shape", rows1)
+    cnt1 = sim.get("support_count")[rows1]
+    assert sim.step(1) == 0, sim.error()
+    gid2 = sim.get("mp_gid")
+    assert np.all(np.diff(gid2) > 0) and np.all(np.diff(sim.get("node_gid")) > 0)
+    st2 = {k: sim.get(k) for k in ("node_x", "node_du", "mp_x", "dF", "F", "be", "sigma", "ebar", "T")}
+    ngid2 = sim.get("node_gid")
+    pos2 = {g: i for i, g in enumerate(gid2)}
+    mat = p.materials[0]
+    checked = plastic = 0
+    for r, q1 in enumerate(rows1):
+        g = gid1[q1]
+        if g not in pos2:
+            continue                      # eroded by the fracture criterion in step 2
+        q2 = pos2[g]
+        nid1 = ngid1[ids1[r, :cnt1[r]]]
+        n2 = np.searchsorted(ngid2, nid1)
+        assert np.array_equal(ngid2[n2], nid1)
+        xp, dF = orc.kinematics(n2.astype(np.int32), shape1[r, :cnt1[r], 0], shape1[r, :cnt1[r], 1:],
+                                st2["node_x"], st2["node_du"])
+        assert np.abs(xp - st2["mp_x"][q2]).max() <= 1e-10 * np.abs(st2["mp_x"]).max()
+        assert np.abs(dF - st2["dF"][q2].reshape(3, 3)).max() <= 1e-10
+        st, sig, be, eb, T, _, failed = orc.return_map(mat, p.dt, st2["dF"][q2].reshape(3, 3), st1["be"][q1],
+                                                       st1["ebar"][q1], st1["T"][q1],
+                                                       np.linalg.det(st2["F"][q2].reshape(3, 3)))
+        assert st == 0 and not failed
+        assert np.abs(sig - st2["sigma"][q2]).max() <= 1e-10 * np.abs(st2["sigma"]).max()
+        assert abs(eb - st2["ebar"][q2]) <= 1e-10 * max(1.0, eb)
+        plastic += eb > 0
+        row = sim.get_rows("support_ids", [q2])[0]
+        n = sim.get_rows("support_count", [q2])[0]
+        sup = brute_support(st2["node_x"], st2["mp_x"][q2], p.rs2)
+        assert np.array_equal(row[:n], sup)
+        s_, N, dN, _, _ = orc.lme(st2["mp_x"][q2] - st2["node_x"][sup], p.beta, p.newton_tol * p.h)
+        assert s_ == 0
+        shp = sim.get_rows("shape", [q2])[0]
+        assert rel(shp[:n, 0], N) <= 1e-10 and rel(shp[:n, 1:], dN) <= 1e-10
+        checked += 1
+    assert checked >= 24 and plastic > 0
+
+
+def test_fullsize_chip_degenerate_embedding_fails_like_the_oracle():
+    """With the tool embedded 3 h at full resolution, the contact projection of step 1 flattens
+    the node layers in front of the rake face so that one MP ends outside the hull of its new
+    support: the Newton solve for lambda cannot converge. The GPU must stop with the same status
+    and the same MP ID as the oracle (stored by tests/golden/make_chip_embedding_failure.py)."""
+    import json
+    import pathlib
+    from paper_2206_08772_gb300.otm import OTM
+    ref = json.loads((pathlib.Path(__file__).parent / "golden" / "chip_embed3h_failure.json").read_text())
+    sim = OTM(chip_full(ref["embed_h"]), precision="fp64", max_support=384)
+    st = sim.step(ref["steps"])
+    assert st == ref["status"]
+    assert sim.error() == (ref["status"], ref["mp_id"])
+
+
+def test_fullsize_adjoint_rod_against_finite_differences():
+    """The adjoint configuration's rod (h 0.29 mm: 38,181 nodes, 202,752 MPs, Johnson-Cook): the
+    GPU adjoint's d(final length, footprint radius)/d(A, B, C, v0) against central differences of
+    the GPU forward (1e-6 relative step) at the forward's arg-max nodes."""
+    from paper_2206_08772_gb300.adjoint import objectives_and_seeds, rod_objectives
+    from paper_2206_08772_gb300.otm import OTM
+
+    def make(theta):
+        A, B, n, C, m, v0 = theta
+        return scenarios.taylor_rod(h=0.29e-3, material=scenarios.copper_jc(A=A, B=B, n=n, C=C, m=m), v0=v0)
+
+    theta0 = np.array([90e6, 292e6, 0.31, 0.025, 1.09, 227.0])
+    steps = 12
+    th = torch.tensor(theta0, dtype=torch.float64, requires_grad=True)
+    vals = rod_objectives(th, make, steps)
+    g = [torch.autograd.grad(vals[o], th, retain_graph=True)[0].numpy() for o in range(2)]
+    base = OTM(make(theta0))
+    assert base.step(steps) == 0
+    _, _, (i_len, i_rad) = objectives_and_seeds(base.get("node_x"), base.get("node_mass"), 0.29e-3)
+    for k in (0, 1, 3, 5):
+        hk = 1e-6 * theta0[k]
+        f = []
+        for sg in (1, -1):
+            t = theta0.copy()
+            t[k] += sg * hk
+            s = OTM(make(t))
+            assert s.step(steps) == 0
+            x = s.get("node_x")
+            f.append((x[i_len, 2], np.hypot(x[i_rad, 0], x[i_rad, 1])))
+        for o in range(2):
+            fd = (f[0][o] - f[1][o]) / (2 * hk)
+            noise = 20 * np.finfo(float).eps * abs(vals[o].item()) / hk
+            assert abs(fd - g[o][k]) <= 1e-6 * abs(g[o][k]) + noise, (k, o, fd, g[o][k])
