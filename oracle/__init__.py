@@ -160,7 +160,7 @@ def params_struct(prob) -> Params:
     P.tool_x0, P.tool_tip_y = c.tool_x0, c.tool_tip_y
     P.tool_rake, P.tool_clear = math.radians(c.tool_rake_deg), math.radians(c.tool_clearance_deg)
     P.tool_v, P.friction = c.tool_velocity, c.friction
-    P.allow_insert = 0
+    P.allow_insert = int(prob.max_insert)
     P.allow_erode = int(any(m.fracture for m in prob.materials))
     for i, m in enumerate(prob.materials):
         P.mat[i] = material_struct(m)

@@ -614,8 +614,10 @@ static void set_err(orc_sim *s, int code, int64_t id)
 }
 
 /* Steps 5 and 6 of Algorithm 1 for every MP: linked-cell search at the current positions,
- * then the LME Newton solve warm-started from the MP's previous lambda. */
-static int search_and_shape(orc_sim *s)
+ * then the LME Newton solve warm-started from the MP's previous lambda. With lme_fail given, an
+ * MP whose Newton solve fails is flagged there (its lambda keeps the warm start) instead of
+ * stopping the step; every other error still stops it. */
+static int search_and_shape(orc_sim *s, uint8_t *lme_fail)
 {
     const orc_params *P = &s->P;
     orc_grid g;
@@ -637,11 +639,26 @@ static int search_and_shape(orc_sim *s)
         s->off[p + 1] = base + cnt;
         for (int64_t k = 0; k < cnt; k++)
             for (int i = 0; i < 3; i++) d[3 * k + i] = s->xp[3 * p + i] - s->x[3 * (int64_t)buf[k] + i];
-        int32_t it = 0;
+        int32_t it = 0, it2 = 0;
+        double lam0[3] = {s->lam[3 * p], s->lam[3 * p + 1], s->lam[3 * p + 2]};
         int lst = orc_lme(cnt, d, P->beta, P->newton_tol * P->h, P->max_newton, s->lam + 3 * p,
                           s->N + base, s->dN + 3 * base, &it);
+        if (lst == ORC_ERR_LME_NOCONV && (lam0[0] != 0.0 || lam0[1] != 0.0 || lam0[2] != 0.0)) {
+            /* a warm start far from the solution can concentrate the weights on a node or two
+             * (singular Hessian): solve once more from lambda = 0 */
+            s->lam[3 * p] = s->lam[3 * p + 1] = s->lam[3 * p + 2] = 0.0;
+            lst = orc_lme(cnt, d, P->beta, P->newton_tol * P->h, P->max_newton, s->lam + 3 * p,
+                          s->N + base, s->dN + 3 * base, &it2);
+            it += it2;
+        }
         s->newton_it[p] = it;
-        if (lst != ORC_OK) { st = lst; set_err(s, st, s->mp_gid[p]); }
+        if (lst == ORC_ERR_LME_NOCONV && lme_fail && cnt > 0) {
+            lme_fail[p] = 1;
+            memcpy(s->lam + 3 * p, lam0, sizeof(lam0));
+        } else if (lst != ORC_OK) {
+            st = lst;
+            set_err(s, st, s->mp_gid[p]);
+        }
     }
     if (st == ORC_OK) s->n_pairs = s->off[s->nm];
     free(buf); free(d); grid_free(&g);
@@ -686,7 +703,7 @@ orc_sim *orc_sim_create(const orc_params *P, int64_t nn, int64_t nm, const doubl
         s->T[p] = P->T0;
     }
     /* Algorithm 1 REQUIRE: support domains and shape functions of the initial sets */
-    s->err = search_and_shape(s);
+    s->err = search_and_shape(s, NULL);
     return s;
 }
 
@@ -746,6 +763,66 @@ static int64_t remove_orphan_nodes(orc_sim *s)
     s->nn = w;
     free(cnt); free(newid);
     return removed;
+}
+
+/* Node insertion. The paper adds nodes to the node set during the run (Sec. 1, Sec. 3.2) but
+ * gives no rule; the reading taken here: an MP whose LME solve fails at its new position lies
+ * outside (or on the boundary of) the convex hull of its support, so a node is inserted one
+ * spacing h beyond the MP, away from the centroid c of its support nodes:
+ *     x_new = x_p + h u / |u|,   u = x_p - c,
+ * which puts x_p strictly inside the hull of the support plus the new node (x_p lies between
+ * c and x_new). The new node is free (no flags), its increment is the MP's own increment of
+ * the step, du = x_p,n+1 - x_p,n (the interpolation of the old support's increments), and
+ * x_prev = x_new - du. New IDs continue the node numbering, in ascending ID of the failing MPs.
+ * At most max_insert nodes are inserted over a run (ORC_ERR_CAPACITY beyond that). */
+#define ORC_INSERT_ROUNDS 1
+static int insert_nodes(orc_sim *s, const uint8_t *lme_fail, int64_t n_fail)
+{
+    const orc_params *P = &s->P;
+    if (s->n_inserted_total + n_fail > P->allow_insert) {
+        for (int64_t p = 0; p < s->nm; p++)
+            if (lme_fail[p]) { set_err(s, ORC_ERR_CAPACITY, s->mp_gid[p]); break; }
+        return ORC_ERR_CAPACITY;
+    }
+    const int64_t nn = s->nn, nn_new = nn + n_fail;
+    if (nn_new > s->cap_nodes) {
+#define GROW(f, k) do { void *q_ = xrealloc(s->f, (size_t)(k) * (size_t)nn_new * sizeof(*s->f)); \
+                        if (!q_) return ORC_ERR_OOM; s->f = q_; } while (0)
+        GROW(x, 3); GROW(x_prev, 3); GROW(du, 3); GROW(mI, 1); GROW(rI, 3); GROW(flags, 1); GROW(node_gid, 1);
+#undef GROW
+        s->cap_nodes = nn_new;
+    }
+    int64_t i = nn;
+    for (int64_t p = 0; p < s->nm; p++) {
+        if (!lme_fail[p]) continue;
+        const double *xp = s->xp + 3 * p;
+        double c[3] = {0.0, 0.0, 0.0};
+        const int64_t n = s->off[p + 1] - s->off[p];
+        for (int64_t k = s->off[p]; k < s->off[p + 1]; k++)
+            for (int d = 0; d < 3; d++) c[d] += s->x[3 * (int64_t)s->ids[k] + d];
+        double u[3], len = 0.0;
+        for (int d = 0; d < 3; d++) {
+            u[d] = xp[d] - c[d] / (double)n;
+            len += u[d] * u[d];
+        }
+        len = sqrt(len);
+        if (!(len > 1e-12 * P->h)) { set_err(s, ORC_ERR_LME_NOCONV, s->mp_gid[p]); return ORC_ERR_LME_NOCONV; }
+        for (int d = 0; d < 3; d++) {
+            const double xn = xp[d] + P->h * (u[d] / len);
+            const double du = xp[d] - s->xp_prev[3 * p + d];
+            s->x[3 * i + d] = xn;
+            s->du[3 * i + d] = du;
+            s->x_prev[3 * i + d] = xn - du;
+            s->rI[3 * i + d] = 0.0;
+        }
+        s->mI[i] = 0.0;
+        s->flags[i] = 0;
+        s->node_gid[i] = s->next_node_gid++;
+        i++;
+    }
+    s->nn = nn_new;
+    s->n_inserted_total += n_fail;
+    return ORC_OK;
 }
 
 /* ------------------------------------------------------------------ public: one step */
@@ -864,8 +941,25 @@ int orc_sim_step(orc_sim *s)
     /* erosion (fracture): failed MPs leave before the new supports are built */
     if (any_failed) s->n_eroded_total += erode_mps(s);
 
-    /* Steps 5-6: search and shape functions at the new configuration */
-    int st = search_and_shape(s);
+    /* Steps 5-6: search and shape functions at the new configuration; with insertion on, MPs
+     * whose solve fails get a node each and the search and solve are repeated once */
+    int st;
+    if (P->allow_insert > 0) {
+        uint8_t *lme_fail = calloc((size_t)s->nm + 1, 1);
+        if (!lme_fail) return ORC_ERR_OOM;
+        for (int round = 0;; round++) {
+            memset(lme_fail, 0, (size_t)s->nm);
+            st = search_and_shape(s, round < ORC_INSERT_ROUNDS ? lme_fail : NULL);
+            if (st != ORC_OK || round == ORC_INSERT_ROUNDS) break;
+            int64_t n_fail = 0;
+            for (int64_t p = 0; p < s->nm; p++) n_fail += lme_fail[p];
+            if (n_fail == 0) break;
+            if ((st = insert_nodes(s, lme_fail, n_fail)) != ORC_OK) break;
+        }
+        free(lme_fail);
+    } else {
+        st = search_and_shape(s, NULL);
+    }
     if (st != ORC_OK) return st;
     if (any_failed && P->allow_erode) s->n_removed_total += remove_orphan_nodes(s);
     return ORC_OK;
@@ -941,7 +1035,7 @@ int orc_sim_refresh(orc_sim *s)
 {
     s->err = ORC_OK;
     s->err_id = 0;
-    s->err = search_and_shape(s);
+    s->err = search_and_shape(s, NULL);
     return s->err;
 }
 

@@ -119,6 +119,7 @@ class Problem:
     newton_tol: float = 1e-13     # LME residual tolerance, relative to h
     max_newton: int = 50
     eps_stab: float = 0.0
+    max_insert: int = 0           # node slots for insertion over the run (0: insertion off)
     steps: int = 100
     seed: int = 0
     meta: dict = field(default_factory=dict)

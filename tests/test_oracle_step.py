@@ -117,3 +117,83 @@ def test_elastic_energy_drift_shrinks_with_dt(orc):
         drifts.append(abs(e1 - e0) / e0)
     assert drifts[0] < 5e-3                 # CFL 0.3, 60 steps
     assert drifts[1] < 0.35 * drifts[0]      # second order in dt
+
+
+def insertion_rod(max_insert=200):
+    p = scenarios.taylor_rod(h=0.8e-3, R=3.2e-3, L=6.4e-3, v0=2000.0, material=scenarios.copper_jc())
+    p.max_insert = max_insert
+    return p
+
+
+def hull_min_weight(pts, x, h):
+    """Largest t such that x = sum w_a pts_a, sum w = 1, all w_a >= t (LP); None if infeasible
+    (x outside the convex hull). t > 0: x strictly inside."""
+    from scipy.optimize import linprog
+    n = pts.shape[0]
+    A = np.hstack([np.vstack([(pts / h).T, np.ones(n)]), np.zeros((4, 1))])
+    b = np.concatenate([x / h, [1.0]])
+    c = np.zeros(n + 1)
+    c[-1] = -1.0
+    r = linprog(c, A_ub=np.hstack([-np.eye(n), np.ones((n, 1))]), b_ub=np.zeros(n), A_eq=A, b_eq=b,
+                bounds=[(0, None)] * n + [(None, 1.0)])
+    return -r.fun if r.status == 0 else None
+
+
+def test_node_insertion_rule(orc):
+    """Node insertion (the paper adds nodes during the run, Sec. 1 and Sec. 3.2, without a rule;
+    the rule taken: a node one spacing beyond an MP whose LME solve fails, away from its support's
+    centroid). At 2000 m/s the rod's foot spreads until MPs leave the hull of their supports at
+    step 34. Pinned independently of the oracle's code: a linear program (scipy) finds each such
+    MP outside the convex hull of its brute-force support before the insertion and strictly inside
+    after it; the new node sits at x_p + h (x_p - c)/|x_p - c| with c the numpy centroid of that
+    support, carries the MP's own increment, takes the next IDs in ascending MP ID; the MP's shape
+    functions then reproduce linear fields (Eq. 14 consistency)."""
+    pytest.importorskip("scipy")
+    p = insertion_rod()
+    sim = orc.Sim(p)
+    n0 = p.n_nodes
+    for k in range(34):
+        before = sim.clone()
+        assert sim.step(1) == 0
+        if sim.counts()["n_nodes"] != n0:
+            break
+    assert k + 1 == 34
+    x, gid = sim.get("node_x"), sim.get("node_gid")
+    xp, mg = sim.get("mp_x"), sim.get("mp_gid")
+    xp_before = before.get("mp_x")
+    new = np.nonzero(gid >= n0)[0]
+    old = np.nonzero(gid < n0)[0]
+    assert new.size >= 1 and np.array_equal(gid[new], n0 + np.arange(new.size))
+    h = p.h
+    owners = []
+    for i in new:
+        dist = np.linalg.norm(xp - x[i], axis=1)
+        q = int(np.argmin(np.abs(dist - h)))
+        assert abs(dist[q] - h) <= 1e-12 * h
+        owners.append(mg[q])
+        d = xp[q] - x[old]
+        sup = old[((d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2]) <= p.rs2]
+        u = xp[q] - x[sup].mean(0)
+        assert np.abs(x[i] - (xp[q] + h * u / np.linalg.norm(u))).max() <= 1e-12 * h
+        assert np.abs(sim.get("node_du")[i] - (xp[q] - xp_before[q])).max() <= 1e-12 * h
+        assert hull_min_weight(x[sup], xp[q], h) is None
+        t = hull_min_weight(x[np.append(sup, i)], xp[q], h)
+        assert t is not None and t > 1e-3
+        # the MP's shape functions on the enlarged support: linear reproducibility
+        off, ids, N, dN = sim.get("offsets"), sim.get("ids"), sim.get("N"), sim.get("dN")
+        a, b = off[q], off[q + 1]
+        assert i in ids[a:b]
+        xa = x[ids[a:b]]
+        assert abs(N[a:b].sum() - 1.0) <= 1e-12
+        assert np.abs(N[a:b] @ xa - xp[q]).max() <= 1e-12 * h
+        assert np.abs(xa.T @ dN[a:b] - np.eye(3)).max() <= 1e-12
+    assert owners == sorted(owners)
+
+
+def test_node_insertion_capacity(orc):
+    """More failing MPs than node slots left: the step stops with CAPACITY at the first one."""
+    p = insertion_rod(max_insert=1)
+    sim = orc.Sim(p)
+    st = sim.step(34)
+    c = sim.counts()
+    assert st == -8 and c["err"] == -8 and c["n_nodes"] == p.n_nodes
