@@ -80,7 +80,8 @@ typedef struct otm_params {
     double wall_p[3], wall_n[3];
     double tool_x0, tool_tip_y, tool_rake, tool_clear, tool_v, friction; /* angles in radians */
     int32_t max_support; /* per-MP support capacity (pair slots per MP), multiple of 32, <= 1024 */
-    int32_t reserved;
+    int32_t max_insert;  /* node slots reserved for node insertion over the run (0: insertion off);
+                          * see otm_step for the insertion rule */
     otm_material mat[4];
 } otm_params;
 
@@ -123,7 +124,20 @@ int otm_init(const otm_problem *prob, const otm_params *params, void *stream, vo
              size_t ws_bytes, otm_handle **out);
 
 /* Advance n_steps explicit steps (Algorithm 1, steps 1-6 each). Synchronises the stream at
- * the end and returns the first error raised by any kernel (later steps are skipped). */
+ * the end and returns the first error raised by any kernel (later steps are skipped).
+ *
+ * Changes of the node and MP sets within a step (the paper adds and removes nodes and MPs,
+ * Sec. 1 and Sec. 3.2, without a rule; these are the rules taken):
+ *  - erosion (allow_erode): MPs that meet the Johnson-Cook fracture criterion (Sec. 4.2) leave
+ *    after the constitutive update; nodes left in no support after the new search are removed.
+ *  - insertion (max_insert > 0): an MP whose LME solve fails at its new position, from the warm
+ *    start and again from lambda = 0, lies outside the hull of its support. A node is inserted
+ *    one spacing h beyond it, away from the centroid c of its support nodes:
+ *    x_new = x_p + h (x_p - c) / |x_p - c|, with increment du = x_p,n+1 - x_p,n (the MP's own
+ *    increment) and no flags; IDs continue the node numbering in ascending MP ID. The search and
+ *    LME then run once more for every MP; a failure there is OTM_ERR_LME_NOCONV. More than
+ *    max_insert insertions over the run give OTM_ERR_CAPACITY.
+ * Both keep every array in ascending ID order (stream compaction, appended IDs). */
 int otm_step(otm_handle *h, int32_t n_steps);
 
 /* Same as otm_step but does not synchronise; errors are reported by otm_error_detail. */

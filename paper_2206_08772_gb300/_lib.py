@@ -55,7 +55,7 @@ class Params(C.Structure):
                 ("wall_p", C.c_double * 3), ("wall_n", C.c_double * 3),
                 ("tool_x0", C.c_double), ("tool_tip_y", C.c_double), ("tool_rake", C.c_double),
                 ("tool_clear", C.c_double), ("tool_v", C.c_double), ("friction", C.c_double),
-                ("max_support", C.c_int32), ("reserved", C.c_int32),
+                ("max_support", C.c_int32), ("max_insert", C.c_int32),
                 ("mat", Material * 4)]
 
 

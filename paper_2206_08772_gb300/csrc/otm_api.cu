@@ -22,8 +22,9 @@ struct otm_handle {
     int32_t *scan_tmp;
     int64_t step;
     long long launches;
-    int64_t n_eroded, n_removed;
-    int64_t nn0, nm0;              // sizes at initialisation (array capacities)
+    int64_t n_eroded, n_removed, n_inserted;
+    int64_t nn0, nm0;              // sizes at initialisation
+    int64_t nn_cap;                // node array capacity (nn0 + max_insert)
     // adjoint
     void *adj_ws;
     bool adj_swap;
@@ -66,11 +67,13 @@ struct PhaseScope {
 static size_t a256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 // Carve every array out of the workspace. With base == NULL only the size is computed.
-static size_t layout(int64_t nn, int64_t nm, int S, int precision, char *base, Dev *D, int32_t **scan_tmp)
+// Node arrays have nn_cap rows (room for inserted nodes); nn is the current count.
+static size_t layout(int64_t nn, int64_t nn_cap, int64_t nm, int S, int precision, char *base, Dev *D,
+                     int32_t **scan_tmp)
 {
     size_t off = 0;
     const int64_t slots = nm * (int64_t)S;
-    const int max_cells = (int)(16 * nn + 65536);
+    const int max_cells = (int)(16 * nn_cap + 65536);
 #define TAKE(ptr, T, count)                                         \
     do {                                                            \
         if (base) (ptr) = (T *)(base + off);                        \
@@ -83,23 +86,23 @@ static size_t layout(int64_t nn, int64_t nm, int S, int precision, char *base, D
     TAKE(d.emax, int, 2);
     TAKE(d.grid, GridDev, 1);
     // nodes
-    TAKE(d.x, double4_32a, nn);
-    TAKE(d.x_prev, double4_32a, nn);
-    TAKE(d.du, double4_32a, nn);
-    TAKE(d.mr, double4_32a, nn);
-    TAKE(d.spos, double4_32a, nn);
-    TAKE(d.spos32, float4, nn);
-    TAKE(d.du32, float4, nn);
-    TAKE(d.nflags, uint8_t, nn);
-    TAKE(d.ngid, int64_t, nn);
-    TAKE(d.ncount, int32_t, nn);
-    TAKE(d.noff, int32_t, nn + 1);
-    TAKE(d.node_cell, int32_t, nn);
-    TAKE(d.node_rank, int32_t, nn);
-    TAKE(d.sorted, int32_t, nn);
+    TAKE(d.x, double4_32a, nn_cap);
+    TAKE(d.x_prev, double4_32a, nn_cap);
+    TAKE(d.du, double4_32a, nn_cap);
+    TAKE(d.mr, double4_32a, nn_cap);
+    TAKE(d.spos, double4_32a, nn_cap);
+    TAKE(d.spos32, float4, nn_cap);
+    TAKE(d.du32, float4, nn_cap);
+    TAKE(d.nflags, uint8_t, nn_cap);
+    TAKE(d.ngid, int64_t, nn_cap);
+    TAKE(d.ncount, int32_t, nn_cap);
+    TAKE(d.noff, int32_t, nn_cap + 1);
+    TAKE(d.node_cell, int32_t, nn_cap);
+    TAKE(d.node_rank, int32_t, nn_cap);
+    TAKE(d.sorted, int32_t, nn_cap);
     TAKE(d.cell_count, int32_t, (int64_t)max_cells + 1);
     TAKE(d.cell_start, int32_t, (int64_t)max_cells + 1);
-    TAKE(tmp, int32_t, scan_tmp_ints((nn > nm ? nn : nm) + 1));
+    TAKE(tmp, int32_t, scan_tmp_ints((nn_cap > nm ? nn_cap : nm) + 1));
     // material points
     TAKE(d.xp, double4_32a, nm);
     TAKE(d.xp_prev, double4_32a, nm);
@@ -119,6 +122,8 @@ static size_t layout(int64_t nn, int64_t nm, int S, int precision, char *base, D
     TAKE(d.cnt, int32_t, nm);
     TAKE(d.newton_it, int32_t, nm);
     TAKE(d.failed, uint8_t, nm);
+    TAKE(d.lme_fail, uint8_t, nm);
+    TAKE(d.n_fail, int32_t, 1);
     TAKE(d.mgid, int64_t, nm);
     // pairs
     TAKE(d.ids, int32_t, slots);
@@ -153,6 +158,7 @@ static int check_params(int64_t nn, int64_t nm, const otm_params *P)
     if (nm * (int64_t)P->max_support >= (int64_t)0x7fffffff) return OTM_ERR_ARG;
     if (nn >= (int64_t)0x7fffffff / 16) return OTM_ERR_ARG;
     if (!(P->eps_stab >= 0.0)) return OTM_ERR_ARG;
+    if (P->max_insert < 0 || nn + P->max_insert >= (int64_t)0x7fffffff / 16) return OTM_ERR_ARG;
     return OTM_OK;
 }
 
@@ -161,7 +167,8 @@ extern "C" int otm_workspace_bytes(int64_t n_nodes, int64_t n_mps, const otm_par
     int st = check_params(n_nodes, n_mps, params);
     if (st != OTM_OK) return st;
     if (!bytes) return OTM_ERR_ARG;
-    *bytes = layout(n_nodes, n_mps, params->max_support, params->precision, nullptr, nullptr, nullptr) + 256;
+    *bytes = layout(n_nodes, n_nodes + params->max_insert, n_mps, params->max_support, params->precision, nullptr,
+                    nullptr, nullptr) + 256;
     return OTM_OK;
 }
 
@@ -207,11 +214,13 @@ static int read_error(otm_handle *h, int32_t *code, int64_t *id)
     return c;
 }
 
-// steps 5-6 of Algorithm 1 plus the node-major lists for the next step's step 1
-static int rebuild_supports(otm_handle *h)
+// steps 5-6 of Algorithm 1 plus the node-major lists for the next step's step 1; with `insert`,
+// MPs whose LME solve fails are flagged for node insertion instead of stopping the step
+static int rebuild_supports(otm_handle *h, bool insert)
 {
     Dev &D = h->D;
     cudaStream_t s = h->stream;
+    D.insert_mode = insert ? 1 : 0;
     {
         PhaseScope ps(h, OTM_PHASE_GRID);
         CK(launch_grid_build(D, s, &h->launches));
@@ -230,7 +239,32 @@ static int rebuild_supports(otm_handle *h)
         PhaseScope ps(h, OTM_PHASE_LME);
         CK(launch_lme(D, s, &h->launches));
     }
+    D.insert_mode = 0;
     return OTM_OK;
+}
+
+// Node insertion after the LME solve of a step (rule in include/otm.h, otm_step): one node per
+// flagged MP, then the search and solve once more for every MP, failures now being errors.
+static int resolve_insertions(otm_handle *h)
+{
+    Dev &D = h->D;
+    cudaStream_t s = h->stream;
+    int32_t nf = 0;
+    CK(cudaMemcpyAsync(&nf, D.n_fail, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (nf == 0) return OTM_OK;
+    {
+        PhaseScope ps(h, OTM_PHASE_COMPACT);
+        if (h->n_inserted + nf > h->P.max_insert) {
+            CK(raise_flagged(D, OTM_ERR_CAPACITY, s, &h->launches));
+        } else {
+            CK(insert_nodes(D, h->scan_tmp, nf, h->nn0 + h->n_inserted, s, &h->launches));
+            h->n_inserted += nf;
+        }
+        CK(cudaMemsetAsync(D.lme_fail, 0, (size_t)D.nm, s));
+        CK(cudaMemsetAsync(D.n_fail, 0, sizeof(int32_t), s));
+    }
+    return rebuild_supports(h, false);
 }
 
 extern "C" int otm_init(const otm_problem *prob, const otm_params *params, void *stream, void *workspace,
@@ -247,7 +281,8 @@ extern "C" int otm_init(const otm_problem *prob, const otm_params *params, void 
     for (int64_t p = 0; p < nm; p++)
         if (prob->mp_material[p] < 0 || prob->mp_material[p] >= params->n_materials) return OTM_ERR_ARG;
     if (((uintptr_t)workspace) & 255) return OTM_ERR_ARG;
-    size_t need = layout(nn, nm, params->max_support, params->precision, nullptr, nullptr, nullptr);
+    const int64_t nn_cap = nn + params->max_insert;
+    size_t need = layout(nn, nn_cap, nm, params->max_support, params->precision, nullptr, nullptr, nullptr);
     if (ws_bytes < need) return OTM_ERR_WORKSPACE;
 
     otm_handle *h = new (std::nothrow) otm_handle();
@@ -256,10 +291,11 @@ extern "C" int otm_init(const otm_problem *prob, const otm_params *params, void 
     h->stream = (cudaStream_t)stream;
     h->ws = workspace;
     h->ws_bytes = ws_bytes;
-    layout(nn, nm, params->max_support, params->precision, (char *)workspace, &h->D, &h->scan_tmp);
+    layout(nn, nn_cap, nm, params->max_support, params->precision, (char *)workspace, &h->D, &h->scan_tmp);
     fill_params(h->D, params);
     h->nn0 = nn;
     h->nm0 = nm;
+    h->nn_cap = nn_cap;
     Dev &D = h->D;
     cudaStream_t s = h->stream;
     int rc = OTM_OK;
@@ -270,7 +306,12 @@ extern "C" int otm_init(const otm_problem *prob, const otm_params *params, void 
             rc = OTM_ERR_ARG;
             break;
         }
-        if (cudaMemsetAsync(D.err, 0xff, sizeof(unsigned long long), s) != cudaSuccess) { rc = OTM_ERR_CUDA; break; }
+        if (cudaMemsetAsync(D.err, 0xff, sizeof(unsigned long long), s) != cudaSuccess ||
+            cudaMemsetAsync(D.lme_fail, 0, (size_t)nm, s) != cudaSuccess ||
+            cudaMemsetAsync(D.n_fail, 0, sizeof(int32_t), s) != cudaSuccess) {
+            rc = OTM_ERR_CUDA;
+            break;
+        }
         if (cudaMemcpyAsync(stage, prob->node_x, 24 * nn, cudaMemcpyHostToDevice, s) != cudaSuccess ||
             launch_pack3to4(stage, nn, D.x, s, &h->launches) != cudaSuccess ||
             cudaMemcpyAsync(stage, prob->node_du0, 24 * nn, cudaMemcpyHostToDevice, s) != cudaSuccess ||
@@ -287,7 +328,7 @@ extern "C" int otm_init(const otm_problem *prob, const otm_params *params, void 
         }
         // the staging copies must land before the region is reused by the support build
         if (cudaStreamSynchronize(s) != cudaSuccess) { rc = OTM_ERR_CUDA; break; }
-        rc = rebuild_supports(h);
+        rc = rebuild_supports(h, false);
         if (rc != OTM_OK) break;
         rc = read_error(h, nullptr, nullptr);
     } while (0);
@@ -331,7 +372,13 @@ static int enqueue_step(otm_handle *h)
         }
         {
             PhaseScope ps(h, OTM_PHASE_LME);
+            D.insert_mode = h->P.max_insert > 0 ? 1 : 0;
             CK(launch_lme(D, s, &h->launches));
+            D.insert_mode = 0;
+        }
+        if (h->P.max_insert > 0) {
+            int rc = resolve_insertions(h);
+            if (rc != OTM_OK) return rc;
         }
         h->step++;
         return OTM_OK;
@@ -351,8 +398,9 @@ static int enqueue_step(otm_handle *h)
         h->n_eroded += eroded;
     }
     // 5-6: linked-cell search, LME shape functions, contributions, node-major lists
-    int rc = rebuild_supports(h);
+    int rc = rebuild_supports(h, h->P.max_insert > 0);
     if (rc != OTM_OK) return rc;
+    if (h->P.max_insert > 0 && (rc = resolve_insertions(h)) != OTM_OK) return rc;
     if (eroded > 0) {      // nodes left in no support are removed
         PhaseScope ps(h, OTM_PHASE_COMPACT);
         int64_t removed = 0;
@@ -557,7 +605,7 @@ extern "C" int otm_refresh(otm_handle *h)
 {
     if (!h) return OTM_ERR_ARG;
     CK(cudaMemsetAsync(h->D.err, 0xff, sizeof(unsigned long long), h->stream));
-    int rc = rebuild_supports(h);
+    int rc = rebuild_supports(h, false);
     if (rc != OTM_OK) return rc;
     return read_error(h, nullptr, nullptr);
 }
@@ -608,7 +656,7 @@ extern "C" void otm_destroy(otm_handle *h)
 // (shape functions, node-major contributions, ranks, offsets): node and MP state, the support
 // lists, and the exponent shift the last LME solve used.
 struct SnapHeader {
-    int64_t nn, nm, step, magic;
+    int64_t nn, nm, step, magic, n_inserted;
 };
 struct SnapField {
     void *p;
@@ -637,7 +685,7 @@ static size_t snap_size(otm_handle *h)
     SnapField f[32];
     const int n = snap_fields(h, f);
     size_t b = 256;
-    for (int i = 0; i < n; i++) b += a256(f[i].row * (size_t)(f[i].kind == 0 ? h->nn0 : h->nm0));
+    for (int i = 0; i < n; i++) b += a256(f[i].row * (size_t)(f[i].kind == 0 ? h->nn_cap : h->nm0));
     return b;
 }
 
@@ -653,13 +701,13 @@ extern "C" int otm_snapshot_save(otm_handle *h, void *dst)
     if (!h || !dst || (((uintptr_t)dst) & 255)) return OTM_ERR_ARG;
     SnapField f[32];
     const int n = snap_fields(h, f);
-    SnapHeader hd = {h->D.nn, h->D.nm, h->step, 0x4f544d53};
+    SnapHeader hd = {h->D.nn, h->D.nm, h->step, 0x4f544d53, h->n_inserted};
     CK(cudaMemcpyAsync(dst, &hd, sizeof(hd), cudaMemcpyHostToDevice, h->stream));
     char *o = (char *)dst + 256;
     for (int i = 0; i < n; i++) {
         const size_t rows = (size_t)(f[i].kind == 0 ? h->D.nn : h->D.nm);
         CK(cudaMemcpyAsync(o, f[i].p, f[i].row * rows, cudaMemcpyDeviceToDevice, h->stream));
-        o += a256(f[i].row * (size_t)(f[i].kind == 0 ? h->nn0 : h->nm0));
+        o += a256(f[i].row * (size_t)(f[i].kind == 0 ? h->nn_cap : h->nm0));
     }
     CK(cudaStreamSynchronize(h->stream));
     return OTM_OK;
@@ -670,17 +718,18 @@ extern "C" int otm_snapshot_load(otm_handle *h, const void *src)
     if (!h || !src || (((uintptr_t)src) & 255)) return OTM_ERR_ARG;
     SnapHeader hd;
     CK(cudaMemcpy(&hd, src, sizeof(hd), cudaMemcpyDeviceToHost));
-    if (hd.magic != 0x4f544d53 || hd.nn > h->nn0 || hd.nm > h->nm0) return OTM_ERR_ARG;
+    if (hd.magic != 0x4f544d53 || hd.nn > h->nn_cap || hd.nm > h->nm0) return OTM_ERR_ARG;
     h->D.nn = hd.nn;
     h->D.nm = hd.nm;
     h->step = hd.step;
+    h->n_inserted = hd.n_inserted;
     SnapField f[32];
     const int n = snap_fields(h, f);
     const char *o = (const char *)src + 256;
     for (int i = 0; i < n; i++) {
         const size_t rows = (size_t)(f[i].kind == 0 ? h->D.nn : h->D.nm);
         CK(cudaMemcpyAsync(f[i].p, o, f[i].row * rows, cudaMemcpyDeviceToDevice, h->stream));
-        o += a256(f[i].row * (size_t)(f[i].kind == 0 ? h->nn0 : h->nm0));
+        o += a256(f[i].row * (size_t)(f[i].kind == 0 ? h->nn_cap : h->nm0));
     }
     Dev &D = h->D;
     // regenerate ranks, offsets, shape functions and contributions: the LME restarts from the
@@ -747,7 +796,7 @@ extern "C" int otm_adjoint_begin(otm_handle *h, void *adj_ws, size_t bytes, cons
     AdjDev A;
     const size_t need = adj_layout(h, nullptr, &A);
     if (bytes < need) return OTM_ERR_WORKSPACE;
-    if (h->P.allow_erode) return OTM_ERR_ARG;   // the adjoint keeps the node and MP sets fixed
+    if (h->P.allow_erode || h->P.max_insert > 0) return OTM_ERR_ARG;   // the adjoint keeps the node and MP sets fixed
     if (h->P.eps_stab != 0.0) return OTM_ERR_ARG;   // the stabilisation term is not differentiated
     h->adj_ws = adj_ws;
     h->adj_swap = false;

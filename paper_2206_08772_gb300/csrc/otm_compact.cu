@@ -1,10 +1,16 @@
-// otm_compact.cu -- erosion as a device stream compaction (Sec. 4.2, Johnson-Cook fracture):
-// material points flagged by the fracture criterion leave the body after the constitutive
-// update of their step, and nodes that belong to no support once the new supports are built are
-// removed. Both compactions are stable (survivors keep ascending ID order): keep flags, an
-// exclusive scan, and a gather of every per-entry array; the support IDs are renumbered through
-// the monotone old->new node map, so rows stay consistent. Scratch comes from regions of the
-// workspace that are dead at that point of the step (see the comments at each call).
+// otm_compact.cu -- changes of the node and MP sets as device stream compactions (the paper adds
+// and removes nodes and MPs during the run, Sec. 1 and Sec. 3.2; erosion by the Johnson-Cook
+// fracture criterion, Sec. 4.2):
+//  - material points flagged by the fracture criterion leave the body after the constitutive
+//    update of their step, and nodes that belong to no support once the new supports are built
+//    are removed. Both compactions are stable (survivors keep ascending ID order): keep flags, an
+//    exclusive scan, and a gather of every per-entry array; the support IDs are renumbered
+//    through the monotone old->new node map, so rows stay consistent.
+//  - node insertion: for each MP whose LME solve failed, a node is appended one spacing beyond
+//    the MP, away from the centroid of its support (slots by an exclusive scan of the failure
+//    flags, so new IDs follow ascending MP ID).
+// Scratch comes from regions of the workspace that are dead at that point of the step (see the
+// comments at each call).
 #include "otm_dev.cuh"
 
 namespace otm {
@@ -160,6 +166,85 @@ cudaError_t remove_orphan_nodes(Dev &D, int32_t *scan_tmp, int64_t *n_drop_host,
         return e;
     D.nn = nn_new;
     return cudaSuccess;
+}
+
+// one warp per MP flagged in lme_fail: the new node at slot nn + slot[p] (see insert_nodes)
+__global__ void k_insert_nodes(const Dev D, const int32_t *slot, int64_t next_gid)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t p = w0; p < D.nm; p += nw) {
+        if (!D.lme_fail[p]) continue;             // warp-uniform
+        const int n = D.cnt[p];
+        const int32_t *row = D.ids + p * (int64_t)D.S;
+        double c0 = 0.0, c1 = 0.0, c2 = 0.0;
+        for (int k = lane; k < n; k += kWarp) {
+            const double4_32a a = D.x[row[k]];
+            c0 += a.x; c1 += a.y; c2 += a.z;
+        }
+        c0 = warp_sum(c0); c1 = warp_sum(c1); c2 = warp_sum(c2);
+        if (lane != 0) continue;
+        const double4_32a xp = D.xp[p], xq = D.xp_prev[p];
+        const double u0 = xp.x - c0 / (double)n, u1 = xp.y - c1 / (double)n, u2 = xp.z - c2 / (double)n;
+        const double len = sqrt(u0 * u0 + u1 * u1 + u2 * u2);
+        const int64_t i = D.nn + slot[p];
+        if (!(len > 1e-12 * D.h) || n <= 0) {
+            raise_error(D.err, OTM_ERR_LME_NOCONV, D.mgid[p]);
+            continue;
+        }
+        const double x0 = xp.x + D.h * (u0 / len), x1 = xp.y + D.h * (u1 / len), x2 = xp.z + D.h * (u2 / len);
+        const double d0 = xp.x - xq.x, d1 = xp.y - xq.y, d2 = xp.z - xq.z;
+        D.x[i] = make_double4_32a(x0, x1, x2, 0.0);
+        D.x_prev[i] = make_double4_32a(x0 - d0, x1 - d1, x2 - d2, 0.0);
+        D.du[i] = make_double4_32a(d0, d1, d2, 0.0);
+        D.du32[i] = make_float4((float)d0, (float)d1, (float)d2, 0.f);
+        D.mr[i] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+        D.nflags[i] = 0;
+        D.ngid[i] = next_gid + slot[p];
+        D.ncount[i] = 0;
+    }
+}
+
+__global__ void k_keep_flag(const uint8_t *flag, int64_t n, int32_t *keep)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        keep[i] = flag[i] ? 1 : 0;
+}
+
+// Append one node per MP flagged in D.lme_fail (n_fail of them; the caller checked the slots).
+// Scratch: the node-major contribution region, which the LME kernel rewrites after the repeated
+// search. D.nn grows by n_fail.
+cudaError_t insert_nodes(Dev &D, int32_t *scan_tmp, int64_t n_fail, int64_t next_gid, cudaStream_t s,
+                         long long *launches)
+{
+    const int64_t nm = D.nm;
+    int32_t *keep = D.precision == OTM_PRECISION_MIXED ? (int32_t *)D.contrib32 : (int32_t *)D.contrib64;
+    int32_t *slot = keep + ((nm + 63) / 64) * 64;
+    k_keep_flag<<<cblocks(nm, 256), 256, 0, s>>>(D.lme_fail, nm, keep);
+    if (launches) *launches += 1;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if ((e = launch_exclusive_scan_tmp(keep, slot, nm, scan_tmp, s, launches)) != cudaSuccess) return e;
+    k_insert_nodes<<<cblocks(nm * 32, 256), 256, 0, s>>>(D, slot, next_gid);
+    if (launches) *launches += 1;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    D.nn += n_fail;
+    return cudaSuccess;
+}
+
+__global__ void k_raise_flagged(const Dev D, int code)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < D.nm; p += (int64_t)gridDim.x * blockDim.x)
+        if (D.lme_fail[p]) raise_error(D.err, code, D.mgid[p]);
+}
+
+// the error `code` for every flagged MP (the smallest ID wins)
+cudaError_t raise_flagged(const Dev &D, int code, cudaStream_t s, long long *launches)
+{
+    k_raise_flagged<<<cblocks(D.nm, 256), 256, 0, s>>>(D, code);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
 }
 
 }  // namespace otm

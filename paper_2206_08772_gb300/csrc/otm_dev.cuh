@@ -40,6 +40,7 @@ struct Dev {
     double h, beta, rs2, cell, dt, tol_abs, eps_stab;
     int max_newton;
     int wall, tool, allow_erode;
+    int insert_mode;                 // 1: an MP whose LME solve fails is flagged for node insertion
     double wall_p[3], wall_n[3];
     double tool_x0, tool_tip_y, tool_rake, tool_clear, tool_v, friction;
     otm_material mat[4];
@@ -59,7 +60,9 @@ struct Dev {
     double4_32a *xp, *xp_prev;       // position and the position of the previous step
     double *F, *dF, *be, *sig, *vol, *mass, *ebar, *T, *rate, *lam, *logz, *logz_in;
     int32_t *mat_id, *cnt, *newton_it;
-    uint8_t *failed;
+    uint8_t *failed;                 // fracture flags of the step
+    uint8_t *lme_fail;               // LME failures of the step (node insertion)
+    int32_t *n_fail;                 // their count
     int64_t *mgid;
     // pairs: MP-major padded rows (ids, shape, rank) and node-major contributions
     int32_t *ids;
@@ -250,6 +253,9 @@ cudaError_t build_search_grid(const double *node_x, int64_t nn, double cell, Sea
 size_t lme_smem_bytes(int S, int warps);
 cudaError_t launch_adjoint_backward(const Dev &D, const AdjDev &A, cudaStream_t s, long long *launches);
 cudaError_t launch_rebuild_ranks(const Dev &D, cudaStream_t s, long long *launches);
+cudaError_t insert_nodes(Dev &D, int32_t *scan_tmp, int64_t n_fail, int64_t next_gid, cudaStream_t s,
+                         long long *launches);
+cudaError_t raise_flagged(const Dev &D, int code, cudaStream_t s, long long *launches);
 cudaError_t erode_mps(Dev &D, int32_t *scan_tmp, int64_t *n_drop_host, cudaStream_t s, long long *launches);
 cudaError_t remove_orphan_nodes(Dev &D, int32_t *scan_tmp, int64_t *n_drop_host, cudaStream_t s,
                                 long long *launches);

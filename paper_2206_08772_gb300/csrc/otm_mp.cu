@@ -543,6 +543,16 @@ __global__ void __launch_bounds__(kLmeWarps * kWarp) k_lme(const Dev D)
         else st = lme_newton_loop(W.dx, W.dy, W.dz, W.q, W.w, cnt, l0, l1, l2, shift0, D.tol_abs, D.max_newton,
                                   lane, T, E, iters);
         if (st == OTM_OK && !lme_jinv(E, inv)) st = OTM_ERR_LME_NOCONV;
+        if (st != OTM_OK && cnt > 0 && (D.lam[3 * p] != 0.0 || D.lam[3 * p + 1] != 0.0 || D.lam[3 * p + 2] != 0.0)) {
+            // a warm start far from the solution can concentrate the weights on a node or two
+            // (singular Hessian): solve once more from lambda = 0
+            l0 = l1 = l2 = 0.0;
+            int it2 = 0;
+            st = lme_newton(W.dx, W.dy, W.dz, W.q, W.w, cnt, l0, l1, l2, shift0, D.tol_abs, D.max_newton, lane, T,
+                            E, it2);
+            iters += it2;
+            if (st == OTM_OK && !lme_jinv(E, inv)) st = OTM_ERR_LME_NOCONV;
+        }
         iZ = 1.0 / E.Z;
         if (lane == 0) {
             D.newton_it[p] = iters;
@@ -550,6 +560,9 @@ __global__ void __launch_bounds__(kLmeWarps * kWarp) k_lme(const Dev D)
                 D.lam[3 * p] = l0; D.lam[3 * p + 1] = l1; D.lam[3 * p + 2] = l2;
                 D.logz_in[p] = shift0;
                 D.logz[p] = E.shift + log(E.Z);
+            } else if (st == OTM_ERR_LME_NOCONV && D.insert_mode && cnt > 0) {
+                D.lme_fail[p] = 1;          // node insertion follows (lambda keeps the warm start)
+                atomicAdd(D.n_fail, 1);
             } else {
                 raise_error(D.err, st, D.mgid[p]);
             }

@@ -51,6 +51,7 @@ def make_params(prob, precision: str = "fp64", max_support: int = 384) -> Params
     P.tool_rake, P.tool_clear = math.radians(c.tool_rake_deg), math.radians(c.tool_clearance_deg)
     P.tool_v, P.friction = c.tool_velocity, c.friction
     P.max_support = max_support
+    P.max_insert = int(getattr(prob, "max_insert", 0))
     for i, m in enumerate(prob.materials):
         P.mat[i] = material_struct(m)
     return P

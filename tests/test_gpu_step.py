@@ -201,3 +201,66 @@ def test_stabilised_residual_matches_oracle(orc, OTM):
     plain = orc.Sim(q)
     assert plain.step(20) == 0
     assert np.abs(plain.get("node_x") - sim_o.get("node_x")).max() > 1e-9
+
+
+def insertion_rod(max_insert=200):
+    p = scenarios.taylor_rod(h=0.8e-3, R=3.2e-3, L=6.4e-3, v0=2000.0, material=scenarios.copper_jc())
+    p.max_insert = max_insert
+    return p
+
+
+def test_node_insertion_matches_oracle(orc, OTM):
+    """Node insertion: at 2000 m/s the rod's foot spreads until MPs leave the hull of their
+    supports (step 34); each gets a node one spacing beyond it. GPU and oracle agree at every step
+    on the node set (IDs bit-exact, inserted ones included), the supports (bit-exact) and, after
+    40 steps, every field (1e-10). The mixed path runs through the same insertions."""
+    p = insertion_rod()
+    sim_o = orc.Sim(p)
+    sim_g = OTM(p, precision="fp64")
+    sim_m = OTM(p, precision="mixed")
+    for k in range(40):
+        assert sim_o.step(1) == 0
+        assert sim_g.step(1) == 0, (k + 1, sim_g.error())
+        assert sim_m.step(1) == 0, (k + 1, sim_m.error())
+        co, cg = sim_o.counts(), sim_g.counts()
+        assert (cg["n_nodes"], cg["n_mps"]) == (co["n_nodes"], co["n_mps"]), f"step {k + 1}"
+        assert np.array_equal(sim_g.get("node_gid"), sim_o.get("node_gid"))
+        assert supports_equal(sim_g, sim_o), f"step {k + 1}"
+    assert sim_o.counts()["n_nodes"] > p.n_nodes
+    assert sim_m.counts()["n_nodes"] == sim_o.counts()["n_nodes"]
+    errs, bad = compare(sim_g, sim_o, {"default": 1e-10})
+    print("insertion", errs)
+    assert not bad, bad
+
+
+def test_node_insertion_capacity(orc, OTM):
+    """One node slot for two failing MPs: both stop at step 34 with CAPACITY at the same MP."""
+    p = insertion_rod(max_insert=1)
+    sim_o = orc.Sim(p)
+    sim_g = OTM(p, precision="fp64")
+    assert sim_o.step(34) == -8
+    assert sim_g.step(34) == -8
+    co = sim_o.counts()
+    assert sim_g.error() == (co["err"], co["err_id"])
+
+
+def test_chip_deep_tool_embedding_inserts_nodes(orc, OTM):
+    """Tool embedded 6 h into the small chip block: the contact projection of step 1 leaves MPs
+    outside their supports' hulls; nodes are inserted (and MPs eroded) in the same step. Node
+    and MP sets, supports and fields agree with the oracle after step 1."""
+    h = 0.02e-3
+    p = scenarios.chip_block(h=h, size=(0.4e-3, 0.2e-3, 0.1e-3), depth=0.06e-3, embed=6 * h, steps=2)
+    p.max_insert = 64
+    sim_o = orc.Sim(p)
+    sim_g = OTM(p, precision="fp64")
+    assert sim_o.step(1) == 0
+    assert sim_g.step(1) == 0, sim_g.error()
+    co, cg = sim_o.counts(), sim_g.counts()
+    assert (cg["n_nodes"], cg["n_mps"]) == (co["n_nodes"], co["n_mps"])
+    assert co["n_nodes"] > p.n_nodes and co["n_mps"] < p.n_mps
+    assert np.array_equal(sim_g.get("node_gid"), sim_o.get("node_gid"))
+    assert np.array_equal(sim_g.get("mp_gid"), sim_o.get("mp_gid"))
+    assert supports_equal(sim_g, sim_o)
+    errs, bad = compare(sim_g, sim_o, {"default": 1e-10})
+    print("chip insertion", errs)
+    assert not bad, bad
