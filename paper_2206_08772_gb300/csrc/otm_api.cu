@@ -281,6 +281,7 @@ extern "C" int otm_init(const otm_problem *prob, const otm_params *params, void 
     for (int64_t p = 0; p < nm; p++)
         if (prob->mp_material[p] < 0 || prob->mp_material[p] >= params->n_materials) return OTM_ERR_ARG;
     if (((uintptr_t)workspace) & 255) return OTM_ERR_ARG;
+    if (exp_table_setup() != cudaSuccess) return OTM_ERR_CUDA;
     const int64_t nn_cap = nn + params->max_insert;
     size_t need = layout(nn, nn_cap, nm, params->max_support, params->precision, nullptr, nullptr, nullptr);
     if (ws_bytes < need) return OTM_ERR_WORKSPACE;
@@ -880,6 +881,7 @@ extern "C" int otm_lme(const double *node_x, const double *mp_x, int64_t n_mps, 
 {
     if (!node_x || !mp_x || !ids || !counts || !lambda || !shape || !status || n_mps < 0) return OTM_ERR_ARG;
     if (max_support < 1 || max_support > kMaxS || !(beta > 0) || !(tol_abs > 0)) return OTM_ERR_ARG;
+    CK(exp_table_setup());
     CK(launch_lme_only(node_x, mp_x, n_mps, ids, counts, max_support, beta, tol_abs, max_newton, lambda, shape,
                        iters, status, (cudaStream_t)stream));
     return OTM_OK;
@@ -888,6 +890,7 @@ extern "C" int otm_lme(const double *node_x, const double *mp_x, int64_t n_mps, 
 extern "C" int otm_exp_selftest(const double *x, int64_t n, double *mine, double *ref, void *stream)
 {
     if (!x || !mine || !ref || n < 0) return OTM_ERR_ARG;
+    CK(exp_table_setup());
     CK(launch_exp_selftest(x, n, mine, ref, (cudaStream_t)stream));
     return OTM_OK;
 }

@@ -237,6 +237,7 @@ cudaError_t launch_search(const Dev &D, cudaStream_t s, long long *launches);
 cudaError_t launch_kin_search(const Dev &D, cudaStream_t s, long long *launches);
 cudaError_t launch_lme(const Dev &D, cudaStream_t s, long long *launches);
 cudaError_t launch_node_offsets(const Dev &D, int32_t *tmp, cudaStream_t s, long long *launches);
+cudaError_t exp_table_setup();
 cudaError_t launch_exp_selftest(const double *x, int64_t n, double *mine, double *ref, cudaStream_t s);
 cudaError_t launch_node_update(const Dev &D, double t_next, cudaStream_t s, long long *launches);
 cudaError_t launch_pack3to4(const double *x3, int64_t n, double4_32a *x4, cudaStream_t s, long long *launches);

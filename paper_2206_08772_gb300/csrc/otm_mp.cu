@@ -11,48 +11,79 @@
 //   k_return_map : Sec. 4.1 / 4.2, thread per MP: Hencky exponential-map radial return (J2
 //                  linear hardening closed form, Johnson-Cook safeguarded Newton), heating,
 //                  fracture flag, sigma = tau / J
+#include <cmath>
+#include <mutex>
+
 #include "otm_dev.cuh"
 #include "otm_rm.cuh"
 
 namespace otm {
 
 // ======================================================================== FP64 exponential
-// exp(x) by Tang's table-driven method (P. T. P. Tang, "Table-driven implementation of the
-// exponential function in IEEE floating-point arithmetic", ACM TOMS 15(2), 1989):
-//   x = (64 m + j) ln2/64 + r, |r| <= ln2/128,  exp(x) = 2^m * 2^(j/64) * exp(r),
-// with n = 64 m + j = round(64 x / ln 2) from the 1.5*2^52 shifter, r by a two-term split of
-// ln2/64 (the high part has 36 significant bits, so n * L1 is exact for |n| < 2^17), and
-// exp(r) - 1 by its Taylor polynomial of degree 5 (truncation below 4e-17 relative). The table
-// 2^(j/64) is filled per block from exp2(). Valid for x in about [-707, 708]; below it returns 0 (a
-// weight below 1e-307 of the largest), above +inf (the caller then re-shifts).
-constexpr double kExpInvL = 0x1.71547652b82fep+6;    // 64 / ln 2
-constexpr double kExpL1 = 0x1.62e42fefa0000p-7;      // ln 2 / 64, high part
-constexpr double kExpL2 = 0x1.cf79abc9e3b3ap-46;     // ln 2 / 64 - kExpL1
+// exp(f) by a table-driven method after P. T. P. Tang ("Table-driven implementation of the
+// exponential function in IEEE floating-point arithmetic", ACM TOMS 15(2), 1989), with the
+// argument scaling folded into the caller: the argument arrives as y = f * 1024 / ln 2 (the LME
+// scales lambda and the prior term instead of every exponent), and
+//   y = n + s, n = round(y) (the 1.5*2^52 shifter), |s| <= 1/2 and exact (Sterbenz),
+//   exp(f) = 2^(n >> 10) * 2^((n & 1023) / 1024) * exp(s ln2 / 1024),
+// with exp(t) - 1 for |t| <= ln2/2048 by its Taylor polynomial of degree 3 (truncation below
+// 5.5e-16 relative). The 1024-entry table 2^(j/1024) is computed once on the host (C library
+// exp2) into g_exp2_table and staged into each block's shared memory. Valid for f in about
+// [-707, 708]; below it returns 0 (a weight below 1e-307 of the largest), above +inf (the caller
+// then re-shifts). The scaling rounds y like any FP64 argument, so the result carries
+// |f| * 2^-53 relative error from it, plus about 3 ulps.
+constexpr int kExpTable = 1024;
+constexpr double kExpScale = 0x1.71547652b82fep+10;   // 1024 / ln 2
+constexpr double kExpC1 = 0x1.62e42fefa39efp-11;      // ln 2 / 1024
+constexpr double kExpC1lo = 0x1.abc9e3b39803fp-66;    // ln 2 / 1024 - kExpC1
+constexpr double kExpC2 = 0x1.ebfbdff82c58fp-23;      // kExpC1^2 / 2
+constexpr double kExpC3 = 0x1.c6b08d704a0c0p-35;      // kExpC1^3 / 6
 constexpr double kExpShifter = 0x1.8p52;
+constexpr int kExpNmin = -1020 * 1024;                 // 2^(n >> 10) stays normal with margin
+constexpr int kExpNmax = 1021 * 1024 + 1023;
 
-__device__ __forceinline__ void exp_table_fill(double *T)
+static __device__ double g_exp2_table[kExpTable];
+
+// Fill g_exp2_table on the current device (first call per device; a synchronous copy, so it
+// belongs before any stream capture: otm_init and the stand-alone entries call it).
+cudaError_t exp_table_setup()
 {
-    for (int j = threadIdx.x; j < 64; j += blockDim.x) T[j] = exp2((double)j / 64.0);
+    static std::mutex mu;
+    static bool done[64];
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done[dev]) return cudaSuccess;
+    double host[kExpTable];
+    for (int j = 0; j < kExpTable; j++) host[j] = std::exp2((double)j / (double)kExpTable);
+    e = cudaMemcpyToSymbol(g_exp2_table, host, sizeof(host));
+    if (e == cudaSuccess) done[dev] = true;
+    return e;
+}
+
+// copy the table into shared memory (block-wide; ends with a barrier)
+__device__ __forceinline__ void exp_table_load(double *T)
+{
+    for (int j = threadIdx.x; j < kExpTable; j += blockDim.x) T[j] = g_exp2_table[j];
     __syncthreads();
 }
 
-__device__ __forceinline__ double exp_tang(double x, const double *T)
+__device__ __forceinline__ double exp_scaled(double y, const double *T)
 {
-    const double t = fma(x, kExpInvL, kExpShifter);
+    const double t = y + kExpShifter;
+    const int hi = __double2hiint(t);
     const int n = __double2loint(t);
-    // range by an integer test on n = round(64 x / ln 2): the result 2^m T_j p stays a normal
-    // double for m = n >> 6 in [-1020, 1021] (x in about [-707, 708]); inputs are finite here
-    // (non-finite positions stop the step before the LME kernel runs)
-    if (n < -65280) return 0.0;
-    if (n > 65400) return INFINITY;
+    // the high word of t is 0x43380000 for round(y) in [0, 2^32) and 0x4337ffff for [-2^32, 0);
+    // a mismatch with the sign of the low word means |y| >= 2^31 (or y is not finite)
+    if (n < kExpNmin || n > kExpNmax || hi != (n < 0 ? 0x4337ffff : 0x43380000)) return (y > 0.0) ? INFINITY : 0.0;
     const double nd = t - kExpShifter;
-    double r = fma(-nd, kExpL1, x);
-    r = fma(-nd, kExpL2, r);
-    const double p = r * fma(r, fma(r, fma(r, fma(r, 1.0 / 120.0, 1.0 / 24.0), 1.0 / 6.0), 0.5), 1.0);
-    const double Tj = T[n & 63];
+    const double sr = y - nd;
+    const double p = sr * fma(sr, fma(sr, kExpC3, kExpC2), kExpC1);
+    const double Tj = T[n & (kExpTable - 1)];
     const double v = fma(Tj, p, Tj);
-    const int m = n >> 6;
-    return __hiloint2double(__double2hiint(v) + (m << 20), __double2loint(v));
+    return __hiloint2double(__double2hiint(v) + ((n >> 10) << 20), __double2loint(v));
 }
 
 // ======================================================================== LME (Eq. 14)
@@ -65,6 +96,7 @@ struct LmeSums {
     double shift;
 };
 
+// q[] and the multipliers passed here are in exponent units of ln2/1024 (see exp_scaled)
 template <bool SHIFTED>
 __device__ __forceinline__ void lme_accumulate(const double *dx, const double *dy, const double *dz, const double *q,
                                                double *w, int n, double l0, double l1, double l2, double qs,
@@ -74,7 +106,7 @@ __device__ __forceinline__ void lme_accumulate(const double *dx, const double *d
         const double x = dx[k], y = dy[k], z = dz[k];
         const double qk = SHIFTED ? q[k] + qs : q[k];
         const double f = fma(l2, z, fma(l1, y, fma(l0, x, qk)));
-        const double wk = exp_tang(f, T);
+        const double wk = exp_scaled(f, T);
         w[k] = wk;
         const double wx = wk * x, wy = wk * y, wz = wk * z;
         v[0] += wk;
@@ -91,13 +123,14 @@ __device__ __forceinline__ void lme_sums(const double *dx, const double *dy, con
     double v[16];
 #pragma unroll
     for (int i = 0; i < 16; i++) v[i] = 0.0;
-    // q[] holds the prior exponent minus the solve's first shift; a different shift (only after
-    // an over/underflow) is applied as a difference
-    const double qs = q0shift - shift;
+    // q[] holds (prior exponent - the solve's first shift) * 1024/ln2; a different shift (only
+    // after an over/underflow) is applied as a difference
+    const double qs = (q0shift - shift) * kExpScale;
+    const double s0 = l0 * kExpScale, s1 = l1 * kExpScale, s2 = l2 * kExpScale;
     if (qs == 0.0)
-        lme_accumulate<false>(dx, dy, dz, q, w, n, l0, l1, l2, qs, lane, T, v);
+        lme_accumulate<false>(dx, dy, dz, q, w, n, s0, s1, s2, qs, lane, T, v);
     else
-        lme_accumulate<true>(dx, dy, dz, q, w, n, l0, l1, l2, qs, lane, T, v);
+        lme_accumulate<true>(dx, dy, dz, q, w, n, s0, s1, s2, qs, lane, T, v);
     const double t = warp_reduce_scatter16(v, lane);   // value j at lanes 2j, 2j+1
     E.Z = __shfl_sync(0xffffffffu, t, 0);
     E.r0 = __shfl_sync(0xffffffffu, t, 2);
@@ -116,9 +149,10 @@ __device__ __forceinline__ double lme_fmax(const double *dx, const double *dy, c
                                            const double *q, int n, double l0, double l1, double l2,
                                            double q0shift, int lane)
 {
+    const double s0 = l0 * kExpScale, s1 = l1 * kExpScale, s2 = l2 * kExpScale;
     double m = -INFINITY;
-    for (int k = lane; k < n; k += kWarp) m = fmax(m, q[k] + (l0 * dx[k] + l1 * dy[k] + l2 * dz[k]));
-    return warp_max(m) + q0shift;
+    for (int k = lane; k < n; k += kWarp) m = fmax(m, q[k] + (s0 * dx[k] + s1 * dy[k] + s2 * dz[k]));
+    return warp_max(m) * (1.0 / kExpScale) + q0shift;
 }
 
 // evaluation with the given shift; if the weights over- or underflow, again with max f
@@ -167,8 +201,8 @@ __device__ __forceinline__ bool logz_less(const LmeSums &t, const LmeSums &c)
 // Damped Newton on the convex log Z(lambda): step -J^-1 (r/Z) = -J'^-1 r, halved until log Z or
 // the residual norm drops; stops when |r| / Z <= tol. All evaluations of one solve share the
 // initial shift (the previous step's log Z, so w ~ N), which makes the log Z comparison a
-// comparison of Z; q[] must hold the prior exponent minus that shift. On return w[] holds the
-// weights of the accepted evaluation E. Warp-uniform.
+// comparison of Z; q[] must hold the prior exponent minus that shift, times 1024/ln2. On return
+// w[] holds the weights of the accepted evaluation E. Warp-uniform.
 // Newton iterations from an evaluation E already taken at lambda (see lme_newton).
 __device__ int lme_newton_loop(const double *dx, const double *dy, const double *dz, const double *q, double *w,
                                int n, double &l0, double &l1, double &l2, double shift, double tol, int max_it,
@@ -208,8 +242,8 @@ __device__ int lme_newton_loop(const double *dx, const double *dy, const double 
 // Damped Newton on the convex log Z(lambda): step -J^-1 (r/Z) = -J'^-1 r, halved until log Z or
 // the residual norm drops; stops when |r| / Z <= tol. All evaluations of one solve share the
 // initial shift (the previous step's log Z, so w ~ N), which makes the log Z comparison a
-// comparison of Z; q[] must hold the prior exponent minus that shift. On return w[] holds the
-// weights of the accepted evaluation E. Warp-uniform.
+// comparison of Z; q[] must hold the prior exponent minus that shift, times 1024/ln2. On return
+// w[] holds the weights of the accepted evaluation E. Warp-uniform.
 __device__ int lme_newton(const double *dx, const double *dy, const double *dz, const double *q, double *w,
                           int n, double &l0, double &l1, double &l2, double shift, double tol, int max_it,
                           int lane, const double *T, LmeSums &E, int &iters)
@@ -342,7 +376,8 @@ struct FirstEval {
 
 size_t lme_smem_bytes(int S, int warps)
 {
-    return 64 * sizeof(double) + (size_t)warps * 5 * (size_t)S * sizeof(double) + (size_t)warps * sizeof(FirstEval);
+    return kExpTable * sizeof(double) + (size_t)warps * 5 * (size_t)S * sizeof(double) +
+           (size_t)warps * sizeof(FirstEval);
 }
 
 size_t search_lme_smem_bytes(int S, int warps) { return lme_smem_bytes(S, warps); }
@@ -470,14 +505,15 @@ __global__ void __launch_bounds__(kLmeWarps * kWarp) k_lme(const Dev D)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double *T = (double *)smem_raw;
-    exp_table_fill(T);
+    exp_table_load(T);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t p = (int64_t)blockIdx.x * kLmeWarps + warp;
     const int S = D.S;
-    FirstEval *FE = (FirstEval *)(smem_raw + 64 * sizeof(double) + (size_t)kLmeWarps * 5 * (size_t)S * sizeof(double));
+    FirstEval *FE =
+        (FirstEval *)(smem_raw + kExpTable * sizeof(double) + (size_t)kLmeWarps * 5 * (size_t)S * sizeof(double));
     // every warp reaches the two block barriers below; idle warps skip the work
     const bool active = (p < D.nm) && !has_error(D.err);
-    WarpSmem W = warp_smem(smem_raw + 64 * sizeof(double), S, warp);
+    WarpSmem W = warp_smem(smem_raw + kExpTable * sizeof(double), S, warp);
     const int64_t base = p * (int64_t)S;
     int cnt = 0;
     double4_32a xp = make_double4_32a(0, 0, 0, 0);
@@ -486,14 +522,16 @@ __global__ void __launch_bounds__(kLmeWarps * kWarp) k_lme(const Dev D)
     if (active) {
         xp = D.xp[p];
         cnt = D.cnt[p];
-        // d_a = x_p - x_a and the prior exponent -beta |d_a|^2, minus the Newton solve's shift
-        const double beta = D.beta;
+        // d_a = x_p - x_a and the prior exponent -beta |d_a|^2, minus the Newton solve's shift,
+        // in units of ln2/1024
+        const double beta_s = D.beta * kExpScale;
         shift0 = D.logz[p];
+        const double shift_s = shift0 * kExpScale;
         for (int k = lane; k < cnt; k += kWarp) {
             const double4_32a a = D.x[D.ids[base + k]];
             const double x = xp.x - a.x, y = xp.y - a.y, z = xp.z - a.z;
             W.dx[k] = x; W.dy[k] = y; W.dz[k] = z;
-            W.q[k] = fma(-beta, fma(z, z, fma(y, y, x * x)), -shift0);
+            W.q[k] = fma(-beta_s, fma(z, z, fma(y, y, x * x)), -shift_s);
         }
         __syncwarp();
         // Eq. 14: the first evaluation at the previous step's lambda (warm start)
@@ -836,11 +874,11 @@ __global__ void __launch_bounds__(kLmeWarps * kWarp)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double *T = (double *)smem_raw;
-    exp_table_fill(T);
+    exp_table_load(T);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t p = (int64_t)blockIdx.x * kLmeWarps + warp;
     if (p >= nm) return;
-    WarpSmem W = warp_smem(smem_raw + 64 * sizeof(double), S, warp);
+    WarpSmem W = warp_smem(smem_raw + kExpTable * sizeof(double), S, warp);
     const int n = counts[p];
     if (n > S || n <= 0) {
         if (lane == 0) atomicCAS(status, 0, n > S ? OTM_ERR_CAPACITY : OTM_ERR_LME_NOCONV);
@@ -852,12 +890,13 @@ __global__ void __launch_bounds__(kLmeWarps * kWarp)
         const int64_t id = ids[base + k];
         const double x = px - node_x[3 * id], y = py - node_x[3 * id + 1], z = pz - node_x[3 * id + 2];
         W.dx[k] = x; W.dy[k] = y; W.dz[k] = z;
-        W.q[k] = -beta * fma(z, z, fma(y, y, x * x));
+        W.q[k] = -(beta * kExpScale) * fma(z, z, fma(y, y, x * x));
     }
     __syncwarp();
     double l0 = lam[3 * p], l1 = lam[3 * p + 1], l2 = lam[3 * p + 2];
     const double shift = lme_fmax(W.dx, W.dy, W.dz, W.q, n, l0, l1, l2, 0.0, lane);
-    for (int k = lane; k < n; k += kWarp) W.q[k] -= shift;
+    const double shift_s = shift * kExpScale;
+    for (int k = lane; k < n; k += kWarp) W.q[k] -= shift_s;
     __syncwarp();
     LmeSums E;
     int iters = 0;
@@ -896,14 +935,20 @@ cudaError_t launch_lme_only(const double *node_x, const double *mp_x, int64_t nm
     return cudaGetLastError();
 }
 
-// self-test of the table-driven exponential against CUDA's exp
-__global__ void k_exp_selftest(const double *x, int64_t n, double *mine, double *ref)
+// self-test of the table-driven exponential: mine = exp_scaled(y); ref = CUDA's exp of the same
+// argument f = y ln2/1024 carried as a + b (a = fl(y c1), b its rounding error plus y times the
+// low part of ln2/1024), ref = exp(a) (1 + b)
+__global__ void k_exp_selftest(const double *y, int64_t n, double *mine, double *ref)
 {
-    __shared__ double T[64];
-    exp_table_fill(T);
+    __shared__ double T[kExpTable];
+    exp_table_load(T);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        mine[i] = exp_tang(x[i], T);
-        ref[i] = exp(x[i]);
+        const double v = y[i];
+        mine[i] = exp_scaled(v, T);
+        const double a = v * kExpC1;
+        const double b = fma(v, kExpC1, -a) + v * kExpC1lo;
+        const double e = exp(a);
+        ref[i] = fma(e, b, e);
     }
 }
 
