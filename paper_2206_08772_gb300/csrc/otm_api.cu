@@ -178,6 +178,7 @@ static void fill_params(Dev &D, const otm_params *P)
     D.beta = P->beta;
     D.rs2 = P->rs2;
     D.cell = P->cell_size;
+    D.sc = make_search_const(P->cell_size, P->rs2);
     D.dt = P->dt;
     D.tol_abs = P->newton_tol * P->h;
     D.eps_stab = P->eps_stab;

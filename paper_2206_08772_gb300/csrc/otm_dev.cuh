@@ -31,6 +31,16 @@ struct GridDev {
     int n_cells;                     // 0 when the grid is invalid (error raised)
 };
 
+// constants of the support search, derived once on the host from the cell size and r_s^2
+struct SearchConst {
+    double cell, rs2;
+    float cf;              // cell size in FP32 (round to nearest)
+    float rs;              // sqrt(rs2) in FP32 (correctly rounded sqrt, then round to nearest)
+    float rs2_rd, rs2_ru;  // rs2 rounded down / up to FP32
+};
+
+SearchConst make_search_const(double cell, double rs2);
+
 struct Dev {
     // sizes and parameters
     int64_t nn, nm;
@@ -38,6 +48,7 @@ struct Dev {
     int precision;
     int max_cells;
     double h, beta, rs2, cell, dt, tol_abs, eps_stab;
+    SearchConst sc;
     int max_newton;
     int wall, tool, allow_erode;
     int insert_mode;                 // 1: an MP whose LME solve fails is flagged for node insertion
@@ -172,6 +183,40 @@ __device__ __forceinline__ double warp_reduce_scatter16(const double (&v)[16], i
     }
     return d + __shfl_xor_sync(0xffffffffu, d, 1);
 }
+
+// Reduce-scatter of 12 per-lane values in 13 additions per lane. Afterwards lane L holds the
+// warp total of value rs12_value(L) = 6 [L & 16] + 3 [L & 8] + (1 if L & 2, else 2 if L & 4,
+// else 0); every value is held by lane pairs (2k, 2k+1), and rs12_writer(L) picks one lane per
+// value.
+__device__ __forceinline__ double warp_reduce_scatter12(const double (&v)[12], int lane)
+{
+    double a[6], b[3];
+#pragma unroll
+    for (int i = 0; i < 6; i++) {
+        const bool up = lane & 16;
+        const double mine = up ? v[6 + i] : v[i], other = up ? v[i] : v[6 + i];
+        a[i] = mine + __shfl_xor_sync(0xffffffffu, other, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        const bool up = lane & 8;
+        const double mine = up ? a[3 + i] : a[i], other = up ? a[i] : a[3 + i];
+        b[i] = mine + __shfl_xor_sync(0xffffffffu, other, 8);
+    }
+    const bool up4 = lane & 4;
+    const double c0 = (up4 ? b[2] : b[0]) + __shfl_xor_sync(0xffffffffu, up4 ? b[0] : b[2], 4);
+    const double c1 = b[1] + __shfl_xor_sync(0xffffffffu, b[1], 4);
+    const bool up2 = lane & 2;
+    const double d = (up2 ? c1 : c0) + __shfl_xor_sync(0xffffffffu, up2 ? c0 : c1, 2);
+    return d + __shfl_xor_sync(0xffffffffu, d, 1);
+}
+
+__device__ __forceinline__ int rs12_value(int lane)
+{
+    return ((lane & 16) ? 6 : 0) + ((lane & 8) ? 3 : 0) + ((lane & 2) ? 1 : ((lane & 4) ? 2 : 0));
+}
+
+__device__ __forceinline__ bool rs12_writer(int lane) { return (lane & 1) == 0 && (lane & 6) != 6; }
 
 __device__ __forceinline__ double warp_max(double v)
 {

@@ -275,16 +275,32 @@ struct SearchGrid {
     const double4_32a *spos;
 };
 
-__device__ int warp_support_search(const SearchGrid &G, double cell, double rs2, double px, double py, double pz,
+SearchConst make_search_const(double cell, double rs2)
+{
+    SearchConst c;
+    c.cell = cell;
+    c.rs2 = rs2;
+    c.cf = (float)cell;
+    c.rs = (float)std::sqrt(rs2);
+    float lo = (float)rs2, hi = (float)rs2;
+    if ((double)lo > rs2) lo = std::nextafterf(lo, -INFINITY);
+    if ((double)hi < rs2) hi = std::nextafterf(hi, INFINITY);
+    c.rs2_rd = lo;
+    c.rs2_ru = hi;
+    return c;
+}
+
+__device__ int warp_support_search(const SearchGrid &G, const SearchConst &C, double px, double py, double pz,
                                    int32_t *list, int S, int lane)
 {
     const GridDev *g = G.g;
     if (g->n_cells == 0) return 0;
     const int nx = g->dims[0], ny = g->dims[1], nz = g->dims[2];
+    const double rs2 = C.rs2;
     // position relative to the grid origin, in FP32 (one FP64 subtraction per axis)
     const float X = (float)(px - g->origin[0]), Y = (float)(py - g->origin[1]), Z = (float)(pz - g->origin[2]);
-    const float cf = (float)cell;
-    const float rs = (float)sqrt(rs2);
+    const float cf = C.cf;
+    const float rs = C.rs;
     // cell ranges covering [x - r_s, x + r_s] with a 1e-4 relative margin (which covers the FP32
     // rounding of X and of the quotient; nodes are binned by the exact FP64 floor)
     const float rsm = rs * 1.0001f;
@@ -301,7 +317,7 @@ __device__ int warp_support_search(const SearchGrid &G, double cell, double rs2,
     const float u = 0x1p-24f;
     const float e = 1.001f * u * (2.f * U + 1.5f * rs);
     const float band = 1.5f * (1.25f * (e * (9.f * rs + 3.f * e) + 3.1f * u * rs * rs) + 1e-15f * rs * rs);
-    const float lo = __fsub_rd(__double2float_rd(rs2), band), hi = __fadd_ru(__double2float_ru(rs2), band);
+    const float lo = __fsub_rd(C.rs2_rd, band), hi = __fadd_ru(C.rs2_ru, band);
     for (int kz = z0; kz <= z1; kz++) {
         for (int ky = y0; ky <= y1; ky++) {
             const int rowc = (kz * ny + ky) * nx;
@@ -394,7 +410,7 @@ __global__ void __launch_bounds__(kSearchWarps * kWarp) k_search(const Dev D)
     int32_t *list = (int32_t *)smem_raw + (size_t)warp * next_pow2(S);
     const double4_32a xp = D.xp[p];
     SearchGrid G{D.grid, D.cell_start, D.spos32, D.spos};
-    const int cnt = warp_support_search(G, D.cell, D.rs2, xp.x, xp.y, xp.z, list, S, lane);
+    const int cnt = warp_support_search(G, D.sc, xp.x, xp.y, xp.z, list, S, lane);
     if (cnt > S) {
         if (lane == 0) {
             raise_error(D.err, OTM_ERR_CAPACITY, D.mgid[p]);
@@ -431,9 +447,9 @@ __global__ void __launch_bounds__(kSearchWarps * kWarp) k_kin_search(const Dev D
     const int S = D.S;
     const int n = D.cnt[p];
     const int64_t base = p * (int64_t)S;
-    double v[16];
+    double v[12];
 #pragma unroll
-    for (int i = 0; i < 16; i++) v[i] = 0.0;
+    for (int i = 0; i < 12; i++) v[i] = 0.0;
     for (int k = lane; k < n; k += kWarp) {
         const int id = D.ids[base + k];
         const double4_32a sh = D.shape[base + k];
@@ -444,12 +460,13 @@ __global__ void __launch_bounds__(kSearchWarps * kWarp) k_kin_search(const Dev D
         v[6] = fma(u.y, sh.y, v[6]); v[7] = fma(u.y, sh.z, v[7]); v[8] = fma(u.y, sh.w, v[8]);
         v[9] = fma(u.z, sh.y, v[9]); v[10] = fma(u.z, sh.z, v[10]); v[11] = fma(u.z, sh.w, v[11]);
     }
-    const double t = warp_reduce_scatter16(v, lane);
-    const int j = lane >> 1;
-    if ((lane & 1) == 0 && j >= 3 && j < 12) {
+    const double t = warp_reduce_scatter12(v, lane);
+    const int j = rs12_value(lane);
+    if (rs12_writer(lane) && j >= 3) {
         const int c = j - 3;
         D.dF[9 * p + c] = (c == 0 || c == 4 || c == 8) ? 1.0 + t : t;
     }
+    // values 0, 1, 2 (x_p) sit at lanes 0, 2, 4
     const double px = __shfl_sync(0xffffffffu, t, 0), py = __shfl_sync(0xffffffffu, t, 2),
                  pz = __shfl_sync(0xffffffffu, t, 4);
     if (lane == 0) {
@@ -460,7 +477,7 @@ __global__ void __launch_bounds__(kSearchWarps * kWarp) k_kin_search(const Dev D
     __syncwarp();   // the old row is read completely before the new support overwrites it
     int32_t *list = (int32_t *)smem_raw + (size_t)warp * next_pow2(S);
     SearchGrid G{D.grid, D.cell_start, D.spos32, D.spos};
-    const int cnt = warp_support_search(G, D.cell, D.rs2, px, py, pz, list, S, lane);
+    const int cnt = warp_support_search(G, D.sc, px, py, pz, list, S, lane);
     if (cnt > S) {
         if (lane == 0) {
             raise_error(D.err, OTM_ERR_CAPACITY, D.mgid[p]);
@@ -722,9 +739,9 @@ __global__ void __launch_bounds__(128) k_kinematics(const Dev D)
     if (has_error(D.err)) return;
     const int n = D.cnt[p];
     const int64_t base = p * (int64_t)D.S;
-    double v[16];
+    double v[12];
 #pragma unroll
-    for (int i = 0; i < 16; i++) v[i] = 0.0;
+    for (int i = 0; i < 12; i++) v[i] = 0.0;
     for (int k = lane; k < n; k += kWarp) {
         const int id = D.ids[base + k];
         const double4_32a sh = D.shape[base + k];
@@ -738,9 +755,9 @@ __global__ void __launch_bounds__(128) k_kinematics(const Dev D)
         v[6] = fma(u1, sh.y, v[6]); v[7] = fma(u1, sh.z, v[7]); v[8] = fma(u1, sh.w, v[8]);
         v[9] = fma(u2, sh.y, v[9]); v[10] = fma(u2, sh.z, v[10]); v[11] = fma(u2, sh.w, v[11]);
     }
-    const double t = warp_reduce_scatter16(v, lane);
-    const int j = lane >> 1;
-    if ((lane & 1) == 0 && j < 12) {
+    const double t = warp_reduce_scatter12(v, lane);
+    const int j = rs12_value(lane);
+    if (rs12_writer(lane)) {
         if (j < 3) {
             ((double *)&D.xp_prev[p])[j] = ((const double *)&D.xp[p])[j];
             ((double *)&D.xp[p])[j] = t;
@@ -820,7 +837,7 @@ cudaError_t launch_return_map(const Dev &D, cudaStream_t s, long long *launches)
 // ======================================================================== stand-alone kernels
 __global__ void __launch_bounds__(kSearchWarps * kWarp)
     k_search_only(const GridDev *g, const int32_t *cell_start, const float4 *spos32, const double4_32a *spos,
-                  double cell, double rs2, const double *mp_x, int64_t nm, int S, int32_t *ids, int32_t *counts,
+                  const SearchConst C, const double *mp_x, int64_t nm, int S, int32_t *ids, int32_t *counts,
                   int32_t *status, const unsigned long long *grid_err)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -838,7 +855,7 @@ __global__ void __launch_bounds__(kSearchWarps * kWarp)
     }
     const double px = mp_x[3 * p], py = mp_x[3 * p + 1], pz = mp_x[3 * p + 2];
     SearchGrid G{g, cell_start, spos32, spos};
-    const int cnt = warp_support_search(G, cell, rs2, px, py, pz, list, S, lane);
+    const int cnt = warp_support_search(G, C, px, py, pz, list, S, lane);
     const int n = min(cnt, S);
     const int Q2 = next_pow2(max(n, 1));
     for (int k = n + lane; k < Q2; k += kWarp) list[k] = 0x7fffffff;
@@ -862,8 +879,9 @@ cudaError_t launch_search_only(const double *node_x, int64_t nn, const double *m
     const size_t smem = (size_t)kSearchWarps * next_pow2(S) * sizeof(int32_t);
     const unsigned blocks = (unsigned)((nm + kSearchWarps - 1) / kSearchWarps);
     if (blocks == 0) return cudaSuccess;
-    k_search_only<<<blocks, kSearchWarps * kWarp, smem, s>>>(V.g, V.cell_start, V.spos32, V.spos, cell, rs2, mp_x,
-                                                             nm, S, ids, counts, status, V.err);
+    k_search_only<<<blocks, kSearchWarps * kWarp, smem, s>>>(V.g, V.cell_start, V.spos32, V.spos,
+                                                             make_search_const(cell, rs2), mp_x, nm, S, ids, counts,
+                                                             status, V.err);
     return cudaGetLastError();
 }
 
