@@ -5,11 +5,17 @@ L 25.4 mm, h 0.12 mm: 501,189 nodes, 2,854,368 material points (synthetic, seede
 pass of Algorithm 1 over all points (node update, kinematics, return map, linked-cell search,
 LME shape functions, node-major lists). Metric: material-point-steps/s = n_mps * steps / time.
 
+The configured run is 1000 steps. The cost of a step grows while the elastic wave from the
+impact sweeps the rod (the LME solve needs Newton iterations wherever the material deforms):
+about 140 ms at step 10, 230 ms at step 500, 260 ms from step 550 on. The timed window therefore
+sits mid-run: --start-step untimed steps (default 500), then W warm-up and K timed steps.
+
 value       : FP64 path, inputs resident in HBM, CUDA events on the library's stream.
-mixed       : the FP32-scatter / FP64-Newton path on the same workload.
+mixed       : the FP32-scatter / FP64-Newton path, from the FP64 path's state at the same step.
 adjoint     : adjoint/forward time ratio of the hand-written GPU adjoint on the 202,752-MP rod.
-e2e         : the same metric through the C ABI with pinned host buffers: otm_init (H2D of the
-              problem + initial supports) + every step followed by a D2H of the node positions.
+e2e         : the same metric through the C ABI from page-locked host memory: the state at the
+              window's start loaded from a host snapshot (H2D of every node, MP and support array),
+              then every step followed by a D2H of the node positions.
 roofline    : the dominant kernel of the step (largest phase time) against its ALU peak.
 cpu_baseline: the serial FP64 oracle on a bounded sample of the same workload (a contiguous
               block of material points in the middle of the rod, with the full node set).
@@ -145,10 +151,20 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------------- GPU arm
-def time_gpu(prob, precision, steps, warmup, torch, dist):
+def time_gpu(prob, precision, steps, warmup, torch, dist, start: int = 0, snap=None, save_snaps: bool = False):
+    """K timed steps after W warm-up steps, from the state after `start` untimed steps (or from
+    the snapshot `snap`). With save_snaps the state there is also returned as a device and a
+    page-locked host snapshot."""
     from paper_2206_08772_gb300.otm import OTM
     sim = OTM(prob, precision=precision)
     stream = sim.stream
+    if snap is not None:
+        sim.restore(snap)
+    elif start > 0:
+        st = sim.step(start)
+        if st != 0:
+            raise RuntimeError(f"spin-up failed: {st} {sim.error()}")
+    snaps = (sim.snapshot(), sim.snapshot(host=True)) if save_snaps else None
     for _ in range(warmup):
         st = sim.step(1)
         if st != 0:
@@ -172,7 +188,8 @@ def time_gpu(prob, precision, steps, warmup, torch, dist):
     launches = sim.launches() - l0
     cnt = sim.get("support_count").astype(np.float64)
     it = sim.get("newton_it").astype(np.float64)
-    info = dict(ms=ms, launches=launches, mean_support=float(cnt.mean()), mean_newton_it=float(it.mean()))
+    info = dict(ms=ms, launches=launches, mean_support=float(cnt.mean()), mean_newton_it=float(it.mean()),
+                snaps=snaps)
     return sim, info
 
 
@@ -188,9 +205,10 @@ def phase_profile(sim, steps: int = 3):
     return {k: (ms / n if n else 0.0) for k, (ms, n) in pt.items()}
 
 
-def time_e2e(prob, precision, steps, torch):
-    """Through the C ABI with pinned host buffers: H2D of the problem inside otm_init, then per
-    step otm_step + a D2H read of the node positions."""
+def time_e2e(prob, precision, steps, torch, host_snap):
+    """Through the C ABI from page-locked host memory: the state at the start of the timed window
+    is loaded from a host snapshot (H2D of every node, MP and support array, then the shape
+    functions regenerated), then per step otm_step + a D2H read of the node positions."""
     from paper_2206_08772_gb300.otm import OTM
 
     def pinned(a):
@@ -198,14 +216,12 @@ def time_e2e(prob, precision, steps, torch):
         t.numpy()[...] = a
         return t.numpy()
 
-    host = dict(node_x=pinned(prob.node_x), node_du0=pinned(prob.node_du0),
-                node_flags=pinned(prob.node_flags), mp_x=pinned(prob.mp_x), mp_vol=pinned(prob.mp_vol),
-                mp_mass=pinned(prob.mp_mass), mp_material=pinned(prob.mp_material.astype(np.int32)))
+    sim = OTM(prob, precision=precision)
     out = pinned(np.zeros((prob.n_nodes, 3)))
-    h2d = sum(v.nbytes for v in host.values())
+    h2d = host_snap[0].numel()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    sim = OTM(prob, precision=precision, host_arrays=host)
+    sim.restore(host_snap)
     for _ in range(steps):
         st = sim.step(1, sync=False)
         if st != 0:
@@ -220,8 +236,8 @@ def time_e2e(prob, precision, steps, torch):
 
 def time_adjoint(steps: int, torch):
     """Adjoint/forward time ratio on the 202,752-MP Johnson-Cook rod (h 0.29 mm): forward of
-    `steps` steps with ceil(sqrt(steps)) checkpoints, then the backward pass (segment recompute +
-    backward steps) for one objective."""
+    `steps` steps from the impact with ceil(sqrt(steps)) checkpoints, then the backward pass
+    (segment recompute + backward steps) for one objective."""
     import math
 
     from paper_2206_08772_gb300.adjoint import backward_pass, objectives_and_seeds
@@ -252,7 +268,9 @@ def time_adjoint(steps: int, torch):
             "objective": "final length", "dL_dtheta": dict(zip(("A", "B", "n", "C", "m", "v0"), grad.tolist()))}
 
 
-def time_oracle(prob, steps: int, warmup: int = 0):
+def time_oracle(prob, steps: int | None, warmup: int = 0, min_seconds: float = 10.0, max_steps: int = 60):
+    """The oracle on the bounded sample: `steps` timed steps, or (steps None) as many as fill
+    min_seconds of CPU time (at most max_steps)."""
     import oracle
     samp = cpu_sample(prob)
     t0 = time.perf_counter()
@@ -261,14 +279,61 @@ def time_oracle(prob, steps: int, warmup: int = 0):
     for _ in range(warmup):
         sim.step(1)
     t0 = time.perf_counter()
-    st = sim.step(steps)
+    if steps is not None:
+        st = sim.step(steps)
+    else:
+        steps = 0
+        st = 0
+        while st == 0 and steps < max_steps and (steps == 0 or time.perf_counter() - t0 < min_seconds):
+            st = sim.step(1)
+            steps += 1
     t = time.perf_counter() - t0
     if st != 0:
         raise RuntimeError(f"oracle step failed {st}")
     return dict(value=samp.n_mps * steps / t, unit=UNIT, cores=1, kind="oracle",
                 sample=(f"{samp.n_mps} MPs (4 cell layers at mid-length) of the {prob.n_mps}-MP rod with all "
-                        f"{prob.n_nodes} nodes, {steps} oracle steps after init ({t_init:.1f} s); serial C, 1 thread"),
+                        f"{prob.n_nodes} nodes, {steps} oracle steps ({t:.1f} s) after init ({t_init:.1f} s), counted "
+                        f"from the impact (early steps: fewer Newton iterations than mid-run); serial C, 1 thread"),
                 seconds=t)
+
+
+def run_sweep(args, torch):
+    """The mixed-precision sweep: 16 Johnson-Cook rods (R 3.2, L 25.4 mm) with h log-spaced from
+    0.5 to 0.12 mm, v0 ~ U(150, 300) m/s, A and B scaled by U(0.9, 1.1) (seeded); each run
+    `sweep_steps` steps in FP64 and in the mixed path. Reported per rod: the time of each path
+    (CUDA events over the steps after 3 warm-up steps) and the final-geometry difference of the
+    mixed path from the FP64 path (which matches the oracle to 1e-10): final length and
+    footprint radius."""
+    from paper_2206_08772_gb300.adjoint import objectives_and_seeds
+    rng = np.random.default_rng(2024)
+    rows = []
+    for i, h in enumerate(np.geomspace(0.5e-3, 0.12e-3, 16)):
+        v0 = float(rng.uniform(150.0, 300.0))
+        A, B = 90e6 * float(rng.uniform(0.9, 1.1)), 292e6 * float(rng.uniform(0.9, 1.1))
+        prob = scenarios.taylor_rod(h=float(h), material=scenarios.copper_jc(A=A, B=B), v0=v0, seed=i,
+                                    name=f"sweep_{i}")
+        res = {}
+        for prec in ("fp64", "mixed"):
+            sim, info = time_gpu(prob, prec, args.sweep_steps, 3, torch, None)
+            L_, R_ = objectives_and_seeds(sim.get("node_x"), sim.get("node_mass"), prob.h)[0]
+            res[prec] = (info["ms"], L_, R_)
+            sim.close()
+            del sim
+            torch.cuda.empty_cache()
+        (t64, L64, R64), (t32, L32, R32) = res["fp64"], res["mixed"]
+        rows.append({"h_mm": float(h) * 1e3, "n_mps": prob.n_mps, "v0": v0, "A": A, "B": B,
+                     "fp64_ms_per_step": t64 / args.sweep_steps, "mixed_ms_per_step": t32 / args.sweep_steps,
+                     "speedup": t64 / t32, "rel_err_length": abs(L32 - L64) / L64,
+                     "rel_err_radius": abs(R32 - R64) / R64})
+        print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    tot64 = sum(r["fp64_ms_per_step"] * r["n_mps"] for r in rows)
+    print(json.dumps({"sweep": "mixed vs fp64, 16 JC rods", "steps": args.sweep_steps + 3, "rods": rows,
+                      "speedup_median": float(np.median([r["speedup"] for r in rows])),
+                      "speedup_weighted": float(sum(r["n_mps"] * r["fp64_ms_per_step"] for r in rows)
+                                                / sum(r["n_mps"] * r["mixed_ms_per_step"] for r in rows)),
+                      "max_rel_err_length": max(r["rel_err_length"] for r in rows),
+                      "max_rel_err_radius": max(r["rel_err_radius"] for r in rows),
+                      "fp64_total_ms_weighted": tot64}))
 
 
 def main():
@@ -282,7 +347,11 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
-    ap.add_argument("--adjoint-steps", type=int, default=46)
+    ap.add_argument("--adjoint-steps", type=int, default=500)
+    ap.add_argument("--start-step", type=int, default=500,
+                    help="untimed steps before the warm-up (the timed window sits mid-run)")
+    ap.add_argument("--sweep", action="store_true", help="run the 16-rod mixed-precision sweep instead")
+    ap.add_argument("--sweep-steps", type=int, default=200)
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -292,7 +361,9 @@ def main():
     config = {"workload": f"{prob.name}: Taylor rod R 3.2 mm, L 25.4 mm, Johnson-Cook copper + adiabatic heating",
               "n_nodes": prob.n_nodes, "n_mps": prob.n_mps, "h_mm": prob.h * 1e3, "gamma": prob.gamma,
               "support_tol": prob.support_tol, "dt_s": prob.dt, "max_support": 384,
-              "l2": "inputs larger than L2 (pair arrays of tens of GB)", "parallelism": f"replicas x{args.gpus}"}
+              "l2": "inputs larger than L2 (pair arrays of tens of GB)", "parallelism": f"replicas x{args.gpus}",
+              "run_steps": 1000, "start_step": args.start_step,
+              "timed_window": f"steps {args.start_step + args.warmup + 1}-{args.start_step + args.warmup + args.steps}"}
 
     if args.impl == "reference":
         if rank != 0:
@@ -318,8 +389,17 @@ def main():
     else:
         torch.cuda.set_device(0)
 
+    if args.sweep:
+        if rank == 0:
+            run_sweep(args, torch)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
     with ClockSampler(local) as clk:
-        sim, info = time_gpu(prob, "fp64", args.steps, args.warmup, torch, dist)
+        sim, info = time_gpu(prob, "fp64", args.steps, args.warmup, torch, dist, start=args.start_step,
+                             save_snaps=True)
+    snap_dev, snap_host = info.pop("snaps")
     phases = phase_profile(sim)
     sim.close()
     del sim
@@ -328,7 +408,7 @@ def main():
 
     mixed = None
     if not args.no_mixed:
-        simm, infom = time_gpu(prob, "mixed", args.steps, args.warmup, torch, dist)
+        simm, infom = time_gpu(prob, "mixed", args.steps, args.warmup, torch, dist, snap=snap_dev)
         phases_m = phase_profile(simm)
         simm.close()
         del simm
@@ -343,7 +423,7 @@ def main():
         torch.cuda.empty_cache()
     e2e = None
     if not args.no_e2e:
-        e2e = time_e2e(prob, "fp64", args.steps, torch)
+        e2e = time_e2e(prob, "fp64", args.steps, torch, snap_host)
         e2e["value"] *= world
     if rank != 0:
         if dist is not None:
@@ -375,7 +455,7 @@ def main():
                 "kernel_ms": kd["ms"], "share_of_step": kd["ms"] / (ms / args.steps), "kernels": kernels}
     cpu = None
     if not args.no_cpu_baseline:
-        o = time_oracle(prob, 2)
+        o = time_oracle(prob, None)
         cpu = {k: o[k] for k in ("value", "unit", "cores", "kind", "sample")}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",

@@ -195,10 +195,13 @@ void otm_destroy(otm_handle *h);
  * function theorem on sum N_a (x_p - x_a) = 0, the return map as isotropic tensor functions).
  * ------------------------------------------------------------------------------------- */
 
-/* Bytes of one snapshot (device memory, 256-byte aligned, caller-owned). */
+/* Bytes of one snapshot (caller-owned, 256-byte aligned; device memory or page-locked host
+ * memory). */
 int otm_snapshot_bytes(otm_handle *h, size_t *bytes);
-/* Copy the complete state into / from a snapshot (device to device). Loading regenerates the
- * shape functions and node-major lists from the stored state, reproducing them exactly. */
+/* Copy the complete state into / from a snapshot. Loading regenerates the shape functions and
+ * node-major lists from the stored state, reproducing them exactly. A snapshot loads into any
+ * handle made with the same problem sizes, max_support and max_insert, of either precision
+ * (otherwise OTM_ERR_ARG); the FP32 increments are rebuilt from the FP64 ones. */
 int otm_snapshot_save(otm_handle *h, void *dst);
 int otm_snapshot_load(otm_handle *h, const void *src);
 

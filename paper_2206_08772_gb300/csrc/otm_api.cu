@@ -116,6 +116,7 @@ static size_t layout(int64_t nn, int64_t nn_cap, int64_t nm, int S, int precisio
     TAKE(d.T, double, nm);
     TAKE(d.rate, double, nm);
     TAKE(d.lam, double, 3 * nm);
+    TAKE(d.lam_prev, double, 3 * nm);
     TAKE(d.logz, double, nm);
     TAKE(d.logz_in, double, nm);
     TAKE(d.mat_id, int32_t, nm);
@@ -217,11 +218,12 @@ static int read_error(otm_handle *h, int32_t *code, int64_t *id)
 
 // steps 5-6 of Algorithm 1 plus the node-major lists for the next step's step 1; with `insert`,
 // MPs whose LME solve fails are flagged for node insertion instead of stopping the step
-static int rebuild_supports(otm_handle *h, bool insert)
+static int rebuild_supports(otm_handle *h, bool insert, int lme_mode)
 {
     Dev &D = h->D;
     cudaStream_t s = h->stream;
     D.insert_mode = insert ? 1 : 0;
+    D.lme_mode = lme_mode;
     {
         PhaseScope ps(h, OTM_PHASE_GRID);
         CK(launch_grid_build(D, s, &h->launches));
@@ -265,7 +267,7 @@ static int resolve_insertions(otm_handle *h)
         CK(cudaMemsetAsync(D.lme_fail, 0, (size_t)D.nm, s));
         CK(cudaMemsetAsync(D.n_fail, 0, sizeof(int32_t), s));
     }
-    return rebuild_supports(h, false);
+    return rebuild_supports(h, false, kLmeKeep);
 }
 
 extern "C" int otm_init(const otm_problem *prob, const otm_params *params, void *stream, void *workspace,
@@ -330,7 +332,7 @@ extern "C" int otm_init(const otm_problem *prob, const otm_params *params, void 
         }
         // the staging copies must land before the region is reused by the support build
         if (cudaStreamSynchronize(s) != cudaSuccess) { rc = OTM_ERR_CUDA; break; }
-        rc = rebuild_supports(h, false);
+        rc = rebuild_supports(h, false, kLmePlain);
         if (rc != OTM_OK) break;
         rc = read_error(h, nullptr, nullptr);
     } while (0);
@@ -375,6 +377,7 @@ static int enqueue_step(otm_handle *h)
         {
             PhaseScope ps(h, OTM_PHASE_LME);
             D.insert_mode = h->P.max_insert > 0 ? 1 : 0;
+            D.lme_mode = kLmeStep;
             CK(launch_lme(D, s, &h->launches));
             D.insert_mode = 0;
         }
@@ -400,7 +403,7 @@ static int enqueue_step(otm_handle *h)
         h->n_eroded += eroded;
     }
     // 5-6: linked-cell search, LME shape functions, contributions, node-major lists
-    int rc = rebuild_supports(h, h->P.max_insert > 0);
+    int rc = rebuild_supports(h, h->P.max_insert > 0, kLmeStep);
     if (rc != OTM_OK) return rc;
     if (h->P.max_insert > 0 && (rc = resolve_insertions(h)) != OTM_OK) return rc;
     if (eroded > 0) {      // nodes left in no support are removed
@@ -607,7 +610,7 @@ extern "C" int otm_refresh(otm_handle *h)
 {
     if (!h) return OTM_ERR_ARG;
     CK(cudaMemsetAsync(h->D.err, 0xff, sizeof(unsigned long long), h->stream));
-    int rc = rebuild_supports(h, false);
+    int rc = rebuild_supports(h, false, kLmePlain);
     if (rc != OTM_OK) return rc;
     return read_error(h, nullptr, nullptr);
 }
@@ -659,6 +662,7 @@ extern "C" void otm_destroy(otm_handle *h)
 // lists, and the exponent shift the last LME solve used.
 struct SnapHeader {
     int64_t nn, nm, step, magic, n_inserted;
+    int64_t nn_cap, nm_cap, S;     // the layout the snapshot was written with
 };
 struct SnapField {
     void *p;
@@ -675,7 +679,8 @@ static int snap_fields(otm_handle *h, SnapField *f)
     f[k++] = {D.nflags, 1, 0}; f[k++] = {D.ngid, 8, 0};
     f[k++] = {D.xp, 32, 1}; f[k++] = {D.xp_prev, 32, 1}; f[k++] = {D.F, 72, 1}; f[k++] = {D.dF, 72, 1}; f[k++] = {D.be, 48, 1};
     f[k++] = {D.sig, 48, 1}; f[k++] = {D.vol, 8, 1}; f[k++] = {D.mass, 8, 1}; f[k++] = {D.ebar, 8, 1};
-    f[k++] = {D.T, 8, 1}; f[k++] = {D.rate, 8, 1}; f[k++] = {D.lam, 24, 1}; f[k++] = {D.logz, 8, 1};
+    f[k++] = {D.T, 8, 1}; f[k++] = {D.rate, 8, 1}; f[k++] = {D.lam, 24, 1}; f[k++] = {D.lam_prev, 24, 1};
+    f[k++] = {D.logz, 8, 1};
     f[k++] = {D.logz_in, 8, 1}; f[k++] = {D.mat_id, 4, 1}; f[k++] = {D.mgid, 8, 1}; f[k++] = {D.cnt, 4, 1};
     f[k++] = {D.newton_it, 4, 1}; f[k++] = {D.failed, 1, 1};
     f[k++] = {D.ids, 4 * S, 1};
@@ -703,12 +708,12 @@ extern "C" int otm_snapshot_save(otm_handle *h, void *dst)
     if (!h || !dst || (((uintptr_t)dst) & 255)) return OTM_ERR_ARG;
     SnapField f[32];
     const int n = snap_fields(h, f);
-    SnapHeader hd = {h->D.nn, h->D.nm, h->step, 0x4f544d53, h->n_inserted};
-    CK(cudaMemcpyAsync(dst, &hd, sizeof(hd), cudaMemcpyHostToDevice, h->stream));
+    SnapHeader hd = {h->D.nn, h->D.nm, h->step, 0x4f544d53, h->n_inserted, h->nn_cap, h->nm0, h->D.S};
+    CK(cudaMemcpyAsync(dst, &hd, sizeof(hd), cudaMemcpyDefault, h->stream));
     char *o = (char *)dst + 256;
     for (int i = 0; i < n; i++) {
         const size_t rows = (size_t)(f[i].kind == 0 ? h->D.nn : h->D.nm);
-        CK(cudaMemcpyAsync(o, f[i].p, f[i].row * rows, cudaMemcpyDeviceToDevice, h->stream));
+        CK(cudaMemcpyAsync(o, f[i].p, f[i].row * rows, cudaMemcpyDefault, h->stream));
         o += a256(f[i].row * (size_t)(f[i].kind == 0 ? h->nn_cap : h->nm0));
     }
     CK(cudaStreamSynchronize(h->stream));
@@ -719,8 +724,10 @@ extern "C" int otm_snapshot_load(otm_handle *h, const void *src)
 {
     if (!h || !src || (((uintptr_t)src) & 255)) return OTM_ERR_ARG;
     SnapHeader hd;
-    CK(cudaMemcpy(&hd, src, sizeof(hd), cudaMemcpyDeviceToHost));
+    CK(cudaStreamSynchronize(h->stream));
+    CK(cudaMemcpy(&hd, src, sizeof(hd), cudaMemcpyDefault));
     if (hd.magic != 0x4f544d53 || hd.nn > h->nn_cap || hd.nm > h->nm0) return OTM_ERR_ARG;
+    if (hd.nn_cap != h->nn_cap || hd.nm_cap != h->nm0 || hd.S != h->D.S) return OTM_ERR_ARG;
     h->D.nn = hd.nn;
     h->D.nm = hd.nm;
     h->step = hd.step;
@@ -730,10 +737,13 @@ extern "C" int otm_snapshot_load(otm_handle *h, const void *src)
     const char *o = (const char *)src + 256;
     for (int i = 0; i < n; i++) {
         const size_t rows = (size_t)(f[i].kind == 0 ? h->D.nn : h->D.nm);
-        CK(cudaMemcpyAsync(f[i].p, o, f[i].row * rows, cudaMemcpyDeviceToDevice, h->stream));
+        CK(cudaMemcpyAsync(f[i].p, o, f[i].row * rows, cudaMemcpyDefault, h->stream));
         o += a256(f[i].row * (size_t)(f[i].kind == 0 ? h->nn_cap : h->nm0));
     }
     Dev &D = h->D;
+    // the FP32 copy of the increments from the FP64 one (a snapshot of either precision path
+    // loads into either)
+    CK(launch_du_to_f32(D, h->stream, &h->launches));
     // regenerate ranks, offsets, shape functions and contributions: the LME restarts from the
     // stored lambda with the stored exponent shift, so it reproduces them exactly
     CK(cudaMemsetAsync(D.err, 0xff, sizeof(unsigned long long), h->stream));
@@ -742,6 +752,7 @@ extern "C" int otm_snapshot_load(otm_handle *h, const void *src)
     CK(launch_rebuild_ranks(D, h->stream, &h->launches));
     CK(launch_node_offsets(D, h->scan_tmp, h->stream, &h->launches));
     CK(cudaMemcpyAsync(D.logz, D.logz_in, (size_t)D.nm * 8, cudaMemcpyDeviceToDevice, h->stream));
+    D.lme_mode = kLmeKeep;
     CK(launch_lme(D, h->stream, &h->launches));
     return read_error(h, nullptr, nullptr);
 }

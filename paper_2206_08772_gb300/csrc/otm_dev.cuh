@@ -31,6 +31,13 @@ struct GridDev {
     int n_cells;                     // 0 when the grid is invalid (error raised)
 };
 
+// where the LME solve of k_lme starts, and what it records:
+//   kLmePlain: at the stored lambda; lam_prev := the solution (initial supports, refresh)
+//   kLmeStep : at 2 lambda_n - lambda_{n-1} (linear extrapolation in time); lam_prev := lambda_n
+//   kLmeKeep : at the stored lambda; lam_prev kept (snapshot restore, the repeated solve after
+//              node insertion)
+constexpr int kLmePlain = 0, kLmeStep = 1, kLmeKeep = 2;
+
 // constants of the support search, derived once on the host from the cell size and r_s^2
 struct SearchConst {
     double cell, rs2;
@@ -52,6 +59,7 @@ struct Dev {
     int max_newton;
     int wall, tool, allow_erode;
     int insert_mode;                 // 1: an MP whose LME solve fails is flagged for node insertion
+    int lme_mode;                    // start of the LME solve, see k_lme (kLmePlain / kLmeStep / kLmeKeep)
     double wall_p[3], wall_n[3];
     double tool_x0, tool_tip_y, tool_rake, tool_clear, tool_v, friction;
     otm_material mat[4];
@@ -70,6 +78,7 @@ struct Dev {
     // material points
     double4_32a *xp, *xp_prev;       // position and the position of the previous step
     double *F, *dF, *be, *sig, *vol, *mass, *ebar, *T, *rate, *lam, *logz, *logz_in;
+    double *lam_prev;                // lambda of the step before (start extrapolation)
     int32_t *mat_id, *cnt, *newton_it;
     uint8_t *failed;                 // fracture flags of the step
     uint8_t *lme_fail;               // LME failures of the step (node insertion)

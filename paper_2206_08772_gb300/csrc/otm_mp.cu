@@ -517,6 +517,23 @@ cudaError_t launch_search(const Dev &D, cudaStream_t s, long long *launches)
 }
 
 // ======================================================================== k_lme
+// store the solution lambda of MP p, and the lambda it replaces where the mode says so
+__device__ __forceinline__ void lme_record(const Dev &D, int64_t p, double l0, double l1, double l2)
+{
+    if (D.lme_mode == kLmeStep) {
+        D.lam_prev[3 * p] = D.lam[3 * p];
+        D.lam_prev[3 * p + 1] = D.lam[3 * p + 1];
+        D.lam_prev[3 * p + 2] = D.lam[3 * p + 2];
+    } else if (D.lme_mode == kLmePlain) {
+        D.lam_prev[3 * p] = l0;
+        D.lam_prev[3 * p + 1] = l1;
+        D.lam_prev[3 * p + 2] = l2;
+    }
+    D.lam[3 * p] = l0;
+    D.lam[3 * p + 1] = l1;
+    D.lam[3 * p + 2] = l2;
+}
+
 template <bool MIXED, bool STAB>
 __global__ void __launch_bounds__(kLmeWarps * kWarp) k_lme(const Dev D)
 {
@@ -551,8 +568,15 @@ __global__ void __launch_bounds__(kLmeWarps * kWarp) k_lme(const Dev D)
             W.q[k] = fma(-beta_s, fma(z, z, fma(y, y, x * x)), -shift_s);
         }
         __syncwarp();
-        // Eq. 14: the first evaluation at the previous step's lambda (warm start)
+        // Eq. 14: the first evaluation at the warm start: the previous step's lambda, or (within
+        // a step) its linear extrapolation in time, which leaves fewer Newton iterations while
+        // the material deforms smoothly
         l0 = D.lam[3 * p]; l1 = D.lam[3 * p + 1]; l2 = D.lam[3 * p + 2];
+        if (D.lme_mode == kLmeStep) {
+            l0 = 2.0 * l0 - D.lam_prev[3 * p];
+            l1 = 2.0 * l1 - D.lam_prev[3 * p + 1];
+            l2 = 2.0 * l2 - D.lam_prev[3 * p + 2];
+        }
         if (cnt > 0) lme_sums_safe(W.dx, W.dy, W.dz, W.q, W.w, cnt, l0, l1, l2, shift0, shift0, lane, T, E);
         if (lane == 0) {
             const double s11[11] = {E.Z, E.r0, E.r1, E.r2, E.a00, E.a11, E.a22, E.a01, E.a12, E.a02, E.shift};
@@ -591,14 +615,16 @@ __global__ void __launch_bounds__(kLmeWarps * kWarp) k_lme(const Dev D)
             D.newton_it[p] = 0;
             D.logz_in[p] = shift0;
             D.logz[p] = FE[warp].logz;
+            lme_record(D, p, l0, l1, l2);
         }
     } else {
-        // Newton iterations (rare with the warm start): per warp, from the first evaluation
+        // Newton iterations: per warp, from the first evaluation
+        const double ws0 = l0, ws1 = l1, ws2 = l2;   // the warm start
         if (cnt <= 0) st = OTM_ERR_LME_NOCONV;
         else st = lme_newton_loop(W.dx, W.dy, W.dz, W.q, W.w, cnt, l0, l1, l2, shift0, D.tol_abs, D.max_newton,
                                   lane, T, E, iters);
         if (st == OTM_OK && !lme_jinv(E, inv)) st = OTM_ERR_LME_NOCONV;
-        if (st != OTM_OK && cnt > 0 && (D.lam[3 * p] != 0.0 || D.lam[3 * p + 1] != 0.0 || D.lam[3 * p + 2] != 0.0)) {
+        if (st != OTM_OK && cnt > 0 && (ws0 != 0.0 || ws1 != 0.0 || ws2 != 0.0)) {
             // a warm start far from the solution can concentrate the weights on a node or two
             // (singular Hessian): solve once more from lambda = 0
             l0 = l1 = l2 = 0.0;
@@ -612,7 +638,7 @@ __global__ void __launch_bounds__(kLmeWarps * kWarp) k_lme(const Dev D)
         if (lane == 0) {
             D.newton_it[p] = iters;
             if (st == OTM_OK) {
-                D.lam[3 * p] = l0; D.lam[3 * p + 1] = l1; D.lam[3 * p + 2] = l2;
+                lme_record(D, p, l0, l1, l2);
                 D.logz_in[p] = shift0;
                 D.logz[p] = E.shift + log(E.Z);
             } else if (st == OTM_ERR_LME_NOCONV && D.insert_mode && cnt > 0) {

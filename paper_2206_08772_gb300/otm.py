@@ -144,11 +144,16 @@ class OTM:
         t = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
         return t, (t.data_ptr() + 255) & ~255
 
-    def snapshot(self):
+    def snapshot(self, host: bool = False):
+        """The complete state in a new buffer: device memory, or page-locked host memory."""
         L = _lib.load()
         nb = C.c_size_t(0)
         check(L.otm_snapshot_bytes(self._h, C.byref(nb)), "otm_snapshot_bytes")
-        buf, ptr = self._aligned(nb.value)
+        if host:
+            buf = torch.empty(nb.value + 256, dtype=torch.uint8, pin_memory=True)
+            ptr = (buf.data_ptr() + 255) & ~255
+        else:
+            buf, ptr = self._aligned(nb.value)
         check(L.otm_snapshot_save(self._h, C.c_void_p(ptr)), "otm_snapshot_save")
         return (buf, ptr)
 
