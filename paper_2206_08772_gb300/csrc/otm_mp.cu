@@ -382,18 +382,110 @@ __device__ __forceinline__ WarpSmem warp_smem(unsigned char *base, int S, int wa
 
 constexpr int kLmeWarps = 4;
 
-// per block: the exp table, the per-warp pair arrays, and the batched first-evaluation records
-struct FirstEval {
-    double sums[11];   // Z, r(3), A(6), shift
-    double inv[6], iZ, logz;
-    int ok;            // 1: converged at the first evaluation, 0: Newton iterations needed
-    int pad;
+// The damped Newton solve of Eq. 14 for the block's MPs, block-synchronous: each round, every
+// warp whose MP has an evaluation pending computes the sums (Z, r, A) at its trial lambda (the
+// pair loop); then one thread per MP takes the scalar decisions (accept or halve the trial, the
+// convergence test, J'^-1, the next Newton step). FP64 instructions cost the pipe the same with
+// one active lane as with 32, so doing the scalar work once per MP instead of once per lane of
+// a warp saves most of it. State of one MP's solve, in shared memory:
+enum : int { kNewtonIdle = 0, kNewtonEval = 1, kNewtonDone = 2, kNewtonFail = 3 };
+struct MpNewton {
+    double E[11];      // sums of the latest evaluation: Z, r (3), A (6), shift
+    double C[11];      // sums at the current (accepted) point
+    double lam[3];     // current lambda
+    double trial[3];   // lambda of the pending evaluation
+    double dir[3];     // Newton direction at the current point
+    double ws[3];      // warm start of the solve (for the cold-start retry)
+    double t;          // step fraction of the pending trial
+    double inv[6];     // J'^-1 at the solution (xx, yy, zz, xy, yz, xz)
+    double iZ, logz;
+    int state, have_cur, iters, iters_total, halvings, retried;
 };
+
+__device__ __forceinline__ LmeSums sums_of(const double *v)
+{
+    LmeSums e;
+    e.Z = v[0]; e.r0 = v[1]; e.r1 = v[2]; e.r2 = v[3];
+    e.a00 = v[4]; e.a11 = v[5]; e.a22 = v[6]; e.a01 = v[7]; e.a12 = v[8]; e.a02 = v[9];
+    e.shift = v[10];
+    return e;
+}
+
+// the solve failed from this start: once more from lambda = 0 if the start was not 0
+__device__ __forceinline__ void newton_fail(MpNewton &m)
+{
+    if (!m.retried && (m.ws[0] != 0.0 || m.ws[1] != 0.0 || m.ws[2] != 0.0)) {
+        m.retried = 1;
+        m.have_cur = 0;
+        m.iters = 0;
+        m.halvings = 0;
+        m.ws[0] = m.ws[1] = m.ws[2] = 0.0;
+        m.trial[0] = m.trial[1] = m.trial[2] = 0.0;
+        m.state = kNewtonEval;
+    } else {
+        m.state = kNewtonFail;
+    }
+}
+
+// one scalar round after an evaluation (the damped Newton of lme_newton_loop, as a state machine)
+__device__ void newton_round(MpNewton &m, double tol, int max_it)
+{
+    if (m.state != kNewtonEval) return;
+    if (!m.have_cur) {               // the first evaluation of a start is the current point
+        for (int i = 0; i < 11; i++) m.C[i] = m.E[i];
+        for (int i = 0; i < 3; i++) m.lam[i] = m.trial[i];
+        m.have_cur = 1;
+    } else {                          // accept if log Z or the residual norm drops, else halve
+        const LmeSums e = sums_of(m.E), c = sums_of(m.C);
+        if (isfinite(e.Z) && (logz_less(e, c) || rn2(e) * (c.Z * c.Z) < rn2(c) * (e.Z * e.Z))) {
+            for (int i = 0; i < 11; i++) m.C[i] = m.E[i];
+            for (int i = 0; i < 3; i++) m.lam[i] = m.trial[i];
+            m.halvings = 0;
+        } else {
+            if (++m.halvings >= 40) {
+                newton_fail(m);
+                return;
+            }
+            m.t *= 0.5;
+            for (int i = 0; i < 3; i++) m.trial[i] = fma(m.t, m.dir[i], m.lam[i]);
+            return;
+        }
+    }
+    const LmeSums c = sums_of(m.C);
+    const double r2 = rn2(c);
+    if (!isfinite(r2) || !isfinite(c.Z)) {
+        newton_fail(m);
+        return;
+    }
+    double inv[6];
+    if (r2 <= tol * tol * c.Z * c.Z) {   // converged: J'^-1, 1/Z and log Z for the outputs
+        if (!lme_jinv(c, inv)) {
+            newton_fail(m);
+            return;
+        }
+        for (int i = 0; i < 6; i++) m.inv[i] = inv[i];
+        m.iZ = 1.0 / c.Z;
+        m.logz = c.shift + log(c.Z);
+        m.state = kNewtonDone;
+        return;
+    }
+    if (m.iters >= max_it || !lme_jinv(c, inv)) {
+        newton_fail(m);
+        return;
+    }
+    m.iters++;
+    m.iters_total++;
+    m.dir[0] = -(inv[0] * c.r0 + inv[3] * c.r1 + inv[5] * c.r2);
+    m.dir[1] = -(inv[3] * c.r0 + inv[1] * c.r1 + inv[4] * c.r2);
+    m.dir[2] = -(inv[5] * c.r0 + inv[4] * c.r1 + inv[2] * c.r2);
+    m.t = 1.0;
+    for (int i = 0; i < 3; i++) m.trial[i] = fma(m.t, m.dir[i], m.lam[i]);
+}
 
 size_t lme_smem_bytes(int S, int warps)
 {
     return kExpTable * sizeof(double) + (size_t)warps * 5 * (size_t)S * sizeof(double) +
-           (size_t)warps * sizeof(FirstEval);
+           (size_t)warps * sizeof(MpNewton);
 }
 
 size_t search_lme_smem_bytes(int S, int warps) { return lme_smem_bytes(S, warps); }
@@ -543,18 +635,17 @@ __global__ void __launch_bounds__(kLmeWarps * kWarp) k_lme(const Dev D)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t p = (int64_t)blockIdx.x * kLmeWarps + warp;
     const int S = D.S;
-    FirstEval *FE =
-        (FirstEval *)(smem_raw + kExpTable * sizeof(double) + (size_t)kLmeWarps * 5 * (size_t)S * sizeof(double));
-    // every warp reaches the two block barriers below; idle warps skip the work
+    MpNewton *NS =
+        (MpNewton *)(smem_raw + kExpTable * sizeof(double) + (size_t)kLmeWarps * 5 * (size_t)S * sizeof(double));
+    // every warp reaches the block barriers below; idle warps skip the work
     const bool active = (p < D.nm) && !has_error(D.err);
     WarpSmem W = warp_smem(smem_raw + kExpTable * sizeof(double), S, warp);
     const int64_t base = p * (int64_t)S;
+    MpNewton &M = NS[warp];
     int cnt = 0;
-    double4_32a xp = make_double4_32a(0, 0, 0, 0);
-    double l0 = 0, l1 = 0, l2 = 0, shift0 = 0;
-    LmeSums E;
+    double shift0 = 0;
     if (active) {
-        xp = D.xp[p];
+        const double4_32a xp = D.xp[p];
         cnt = D.cnt[p];
         // d_a = x_p - x_a and the prior exponent -beta |d_a|^2, minus the Newton solve's shift,
         // in units of ln2/1024
@@ -567,88 +658,68 @@ __global__ void __launch_bounds__(kLmeWarps * kWarp) k_lme(const Dev D)
             W.dx[k] = x; W.dy[k] = y; W.dz[k] = z;
             W.q[k] = fma(-beta_s, fma(z, z, fma(y, y, x * x)), -shift_s);
         }
-        __syncwarp();
-        // Eq. 14: the first evaluation at the warm start: the previous step's lambda, or (within
-        // a step) its linear extrapolation in time, which leaves fewer Newton iterations while
-        // the material deforms smoothly
-        l0 = D.lam[3 * p]; l1 = D.lam[3 * p + 1]; l2 = D.lam[3 * p + 2];
-        if (D.lme_mode == kLmeStep) {
-            l0 = 2.0 * l0 - D.lam_prev[3 * p];
-            l1 = 2.0 * l1 - D.lam_prev[3 * p + 1];
-            l2 = 2.0 * l2 - D.lam_prev[3 * p + 2];
-        }
-        if (cnt > 0) lme_sums_safe(W.dx, W.dy, W.dz, W.q, W.w, cnt, l0, l1, l2, shift0, shift0, lane, T, E);
         if (lane == 0) {
-            const double s11[11] = {E.Z, E.r0, E.r1, E.r2, E.a00, E.a11, E.a22, E.a01, E.a12, E.a02, E.shift};
-            for (int i = 0; i < 11; i++) FE[warp].sums[i] = (cnt > 0) ? s11[i] : 0.0;
+            // Eq. 14: the warm start is the previous step's lambda, or (within a step) its
+            // linear extrapolation in time, which leaves fewer Newton iterations while the
+            // material deforms smoothly
+            double l0 = D.lam[3 * p], l1 = D.lam[3 * p + 1], l2 = D.lam[3 * p + 2];
+            if (D.lme_mode == kLmeStep) {
+                l0 = 2.0 * l0 - D.lam_prev[3 * p];
+                l1 = 2.0 * l1 - D.lam_prev[3 * p + 1];
+                l2 = 2.0 * l2 - D.lam_prev[3 * p + 2];
+            }
+            M.trial[0] = M.ws[0] = l0;
+            M.trial[1] = M.ws[1] = l1;
+            M.trial[2] = M.ws[2] = l2;
+            M.t = 1.0;
+            M.have_cur = M.iters = M.iters_total = M.halvings = M.retried = 0;
+            M.state = cnt > 0 ? kNewtonEval : kNewtonFail;
         }
+    } else if (lane == 0) {
+        M.state = kNewtonIdle;
     }
     __syncthreads();
-    // the convergence test, J'^-1, 1/Z and log Z of the block's MPs, one lane per MP
-    if (warp == 0 && lane < kLmeWarps) {
-        const int64_t q = (int64_t)blockIdx.x * kLmeWarps + lane;
-        FirstEval &f = FE[lane];
-        f.ok = 0;
-        if (q < D.nm) {
-            LmeSums e;
-            e.Z = f.sums[0]; e.r0 = f.sums[1]; e.r1 = f.sums[2]; e.r2 = f.sums[3];
-            e.a00 = f.sums[4]; e.a11 = f.sums[5]; e.a22 = f.sums[6]; e.a01 = f.sums[7]; e.a12 = f.sums[8];
-            e.a02 = f.sums[9]; e.shift = f.sums[10];
-            const double r2 = rn2(e);
-            const double tol = D.tol_abs;
-            if (e.Z > 0.0 && isfinite(r2) && isfinite(e.Z) && r2 <= tol * tol * e.Z * e.Z && lme_jinv(e, f.inv)) {
-                f.ok = 1;
-                f.iZ = 1.0 / e.Z;
-                f.logz = e.shift + log(e.Z);
+    // rounds: evaluations of the pending trials, then the scalar decisions
+    for (;;) {
+        if (M.state == kNewtonEval) {
+            __syncwarp();
+            LmeSums E;
+            // trials share the current point's exponent shift (the first one: the solve's shift)
+            const double sh = M.have_cur ? M.C[10] : shift0;
+            lme_sums_safe(W.dx, W.dy, W.dz, W.q, W.w, cnt, M.trial[0], M.trial[1], M.trial[2], sh, shift0, lane, T,
+                          E);
+            __syncwarp();
+            if (lane == 0) {
+                const double s11[11] = {E.Z, E.r0, E.r1, E.r2, E.a00, E.a11, E.a22, E.a01, E.a12, E.a02, E.shift};
+                for (int i = 0; i < 11; i++) M.E[i] = s11[i];
             }
         }
+        __syncthreads();
+        bool pending = false;
+        if (warp == 0 && lane < kLmeWarps) {
+            newton_round(NS[lane], D.tol_abs, D.max_newton);
+            pending = NS[lane].state == kNewtonEval;
+        }
+        if (!__syncthreads_or(pending)) break;
     }
-    __syncthreads();
     if (!active) return;
-    double inv[6], iZ;
-    int iters = 0;
-    int st = OTM_OK;
-    if (FE[warp].ok) {
-        for (int i = 0; i < 6; i++) inv[i] = FE[warp].inv[i];
-        iZ = FE[warp].iZ;
-        if (lane == 0) {
-            D.newton_it[p] = 0;
+    const int st = M.state == kNewtonDone ? OTM_OK : OTM_ERR_LME_NOCONV;
+    if (lane == 0) {
+        D.newton_it[p] = M.iters_total;
+        if (st == OTM_OK) {
+            lme_record(D, p, M.lam[0], M.lam[1], M.lam[2]);
             D.logz_in[p] = shift0;
-            D.logz[p] = FE[warp].logz;
-            lme_record(D, p, l0, l1, l2);
-        }
-    } else {
-        // Newton iterations: per warp, from the first evaluation
-        const double ws0 = l0, ws1 = l1, ws2 = l2;   // the warm start
-        if (cnt <= 0) st = OTM_ERR_LME_NOCONV;
-        else st = lme_newton_loop(W.dx, W.dy, W.dz, W.q, W.w, cnt, l0, l1, l2, shift0, D.tol_abs, D.max_newton,
-                                  lane, T, E, iters);
-        if (st == OTM_OK && !lme_jinv(E, inv)) st = OTM_ERR_LME_NOCONV;
-        if (st != OTM_OK && cnt > 0 && (ws0 != 0.0 || ws1 != 0.0 || ws2 != 0.0)) {
-            // a warm start far from the solution can concentrate the weights on a node or two
-            // (singular Hessian): solve once more from lambda = 0
-            l0 = l1 = l2 = 0.0;
-            int it2 = 0;
-            st = lme_newton(W.dx, W.dy, W.dz, W.q, W.w, cnt, l0, l1, l2, shift0, D.tol_abs, D.max_newton, lane, T,
-                            E, it2);
-            iters += it2;
-            if (st == OTM_OK && !lme_jinv(E, inv)) st = OTM_ERR_LME_NOCONV;
-        }
-        iZ = 1.0 / E.Z;
-        if (lane == 0) {
-            D.newton_it[p] = iters;
-            if (st == OTM_OK) {
-                lme_record(D, p, l0, l1, l2);
-                D.logz_in[p] = shift0;
-                D.logz[p] = E.shift + log(E.Z);
-            } else if (st == OTM_ERR_LME_NOCONV && D.insert_mode && cnt > 0) {
-                D.lme_fail[p] = 1;          // node insertion follows (lambda keeps the warm start)
-                atomicAdd(D.n_fail, 1);
-            } else {
-                raise_error(D.err, st, D.mgid[p]);
-            }
+            D.logz[p] = M.logz;
+        } else if (D.insert_mode && cnt > 0) {
+            D.lme_fail[p] = 1;          // node insertion follows (lambda keeps the warm start)
+            atomicAdd(D.n_fail, 1);
+        } else {
+            raise_error(D.err, st, D.mgid[p]);
         }
     }
+    double inv[6];
+    for (int i = 0; i < 6; i++) inv[i] = M.inv[i];
+    const double iZ = M.iZ;
     if (st != OTM_OK) return;
 
     // N_a = w_a / Z, grad N_a = -N_a J^-1 d_a = -w_a J'^-1 d_a; contributions for Eq. 5 of the next
