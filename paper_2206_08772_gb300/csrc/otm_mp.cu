@@ -906,6 +906,7 @@ __global__ void __launch_bounds__(128) k_return_map(const Dev D)
     for (int i = 0; i < 6; i++) in.be[i] = D.be[6 * p + i];
     in.ebar = D.ebar[p];
     in.T = D.T[p];
+    in.guess = D.rate[p] * D.dt;   // the previous step's plastic increment
     RmOut o;
     const int st = return_map_point(D.mat[D.mat_id[p]], D.dt, in, o);
     if (st != OTM_OK) {
@@ -1084,6 +1085,7 @@ __global__ void __launch_bounds__(128)
     for (int i = 0; i < 6; i++) in.be[i] = be[6 * p + i];
     in.ebar = ebar[p];
     in.T = T[p];
+    in.guess = 0.0;
     const double *Fn = F_new + 9 * p;
     in.J = Fn[0] * (Fn[4] * Fn[8] - Fn[5] * Fn[7]) - Fn[1] * (Fn[3] * Fn[8] - Fn[5] * Fn[6]) +
            Fn[2] * (Fn[3] * Fn[7] - Fn[4] * Fn[6]);

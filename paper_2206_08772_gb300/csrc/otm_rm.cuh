@@ -43,26 +43,35 @@ __device__ inline void jacobi_sym3(double A[3][3], double V[3][3])
     }
 }
 
+// the thermal softening factor 1 - T*^m of the Johnson-Cook flow stress (T* clamped to [0, 1])
+__device__ __forceinline__ double jc_therm(const otm_material &M, double T)
+{
+    const double tstar = fmin(fmax((T - M.T_room) / (M.T_melt - M.T_room), 0.0), 1.0);
+    return 1.0 - pow(tstar, M.m);
+}
+
+// Johnson-Cook flow stress at ebar_n + x with plastic rate x / dt, and its derivative in x;
+// `therm` from jc_therm (the temperature is held at T_n within the step)
 __device__ __forceinline__ void jc_sigma_y(const otm_material &M, double ebar_n, double x, double dt,
-                                           double T, double &sy, double &dsy)
+                                           double therm, double &sy, double &dsy)
 {
     const double ebar = ebar_n + x;
-    const double tstar = fmin(fmax((T - M.T_room) / (M.T_melt - M.T_room), 0.0), 1.0);
-    const double therm = 1.0 - pow(tstar, M.m);
     const double rstar = (x / dt) / M.eps_dot0;
     double rate = 1.0, drate = 0.0;
     if (rstar > 1.0) {
         rate = 1.0 + M.C * log(rstar);
         drate = M.C / x;
     }
-    const double hard = M.A + M.B * pow(ebar, M.n);
-    const double dhard = (ebar > 0.0) ? M.B * M.n * pow(ebar, M.n - 1.0) : INFINITY;
+    const double pe = pow(ebar, M.n);
+    const double hard = M.A + M.B * pe;
+    const double dhard = (ebar > 0.0) ? M.B * M.n * pe / ebar : INFINITY;
     sy = hard * rate * therm;
     dsy = (dhard * rate + hard * drate) * therm;
 }
 
 struct RmIn {
     double dF[9], be[6], ebar, T, J;
+    double guess;      // start of the consistency iteration (e.g. the last step's increment); <= 0: none
 };
 struct RmOut {
     double sig[6], be[6], ebar, T, rate;
@@ -107,15 +116,19 @@ __device__ inline int return_map_point(const otm_material &M, double dt, const R
         const double f_tr = sn - 0.81649658092772603273 * (M.sigma_y0 + M.H * in.ebar);
         if (f_tr > 0.0) dep = 0.81649658092772603273 * f_tr / (2.0 * mu + 2.0 * M.H / 3.0);
     } else {
+        const double therm = jc_therm(M, in.T);
         double sy0, dsy0;
-        jc_sigma_y(M, in.ebar, 0.0, dt, in.T, sy0, dsy0);
+        jc_sigma_y(M, in.ebar, 0.0, dt, therm, sy0, dsy0);
         if (q_tr - sy0 > 0.0) {
-            double lo = 0.0, hi = q_tr / (3.0 * mu), x = 0.5 * hi;
+            // g(x) = q_tr - 3 mu x - sigma_y(x) on [0, q_tr / (3 mu)]: Newton safeguarded by
+            // bisection, from the given guess when it lies inside the bracket
+            double lo = 0.0, hi = q_tr / (3.0 * mu);
+            double x = (in.guess > 0.0 && in.guess < hi) ? in.guess : 0.5 * hi;
             const double tol = 1e-12 * q_tr;
             bool ok = false;
             for (int it = 0; it < 300; it++) {
                 double sy, dsy;
-                jc_sigma_y(M, in.ebar, x, dt, in.T, sy, dsy);
+                jc_sigma_y(M, in.ebar, x, dt, therm, sy, dsy);
                 const double g = q_tr - 3.0 * mu * x - sy;
                 if (fabs(g) <= tol) { ok = true; break; }
                 if (g > 0.0) lo = x; else hi = x;
