@@ -54,6 +54,10 @@ UNIT = "MP-steps/s"
 LME_PER_PAIR_SETUP, LME_PER_PAIR_EVAL, LME_PER_PAIR_FINAL = 8, 44, 39
 SEARCH_PER_CAND, CAND_PER_PAIR = 8, 3.73
 KIN_PER_PAIR = 24
+# DRAM bytes per pair of one k_lme launch, from the ncu capture of the h 0.29 mm rod at step 302
+# (dram__bytes_read.sum + dram__bytes_write.sum = 3.805 GB over 54.11 M pairs); the traffic of
+# a launch scales with its pairs (shape and contribution writes, ID and rank reads)
+LME_DRAM_BYTES_PER_PAIR = 3.804805e9 / (202752 * 266.871)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 2 FP64 FMA lanes / SM / clock at 2070 MHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
@@ -449,7 +453,10 @@ def main():
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
     kd = kernels[dom]
     roofline = {"kernel": f"k_{dom}", "bound": "alu", "achieved": kd["achieved_tflops"], "peak": kd["peak"],
-                "unit": "TFLOP/s", "frac": kd["frac"], "traffic": None,
+                "unit": "TFLOP/s", "frac": kd["frac"],
+                "traffic": LME_DRAM_BYTES_PER_PAIR * pairs if dom == "lme" else None,
+                "traffic_note": ("bytes per launch: DRAM bytes per pair of the ncu capture on the 202,752-MP rod "
+                                 "(profiles/step_kernels_taylor_jc_h0.29.md) x this launch's pairs"),
                 "peak_source": ("derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz (probe measured 1.20)"
                                 if kd["kind"] == "fp64" else "derived: 152 SMs x 128 FP32 FMA/clk x 2 x 2070 MHz"),
                 "kernel_ms": kd["ms"], "share_of_step": kd["ms"] / (ms / args.steps), "kernels": kernels}
