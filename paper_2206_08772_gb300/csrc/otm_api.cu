@@ -135,6 +135,11 @@ static size_t layout(int64_t nn, int64_t nn_cap, int64_t nm, int S, int precisio
         TAKE(d.contrib64, double4_32a, slots);
     }
     TAKE(d.rank, uint16_t, slots);
+    // staging of state transfers: up to 32 MiB, at least one 72-byte row
+    size_t stage = (size_t)24 * (size_t)(nn_cap > nm ? nn_cap : nm);
+    if (stage > ((size_t)32 << 20)) stage = (size_t)32 << 20;
+    if (stage < 256) stage = 256;
+    TAKE(d.stage, char, stage);
 #undef TAKE
     if (base) {
         d.nn = nn;
@@ -142,6 +147,7 @@ static size_t layout(int64_t nn, int64_t nn_cap, int64_t nm, int S, int precisio
         d.S = S;
         d.precision = precision;
         d.max_cells = max_cells;
+        d.stage_bytes = stage;
         *D = d;
         *scan_tmp = tmp;
     }
@@ -504,6 +510,32 @@ static bool field_view(otm_handle *h, int32_t f, FieldView *v)
     }
 }
 
+// device rows (pitch) <-> dense host rows (width), through the staging buffer in chunks
+static int rows_d2h(otm_handle *h, const void *src, size_t pitch, size_t width, size_t rows, void *host_dst)
+{
+    const size_t chunk = h->D.stage_bytes / width;
+    for (size_t r0 = 0; r0 < rows; r0 += chunk) {
+        const size_t n = (rows - r0 < chunk) ? rows - r0 : chunk;
+        CK(launch_rows_to_dense((const char *)src + r0 * pitch, pitch, width, (int64_t)n, h->D.stage, h->stream));
+        CK(cudaMemcpyAsync((char *)host_dst + r0 * width, h->D.stage, n * width, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+    }
+    return OTM_OK;
+}
+
+static int rows_h2d(otm_handle *h, const void *host_src, size_t pitch, size_t width, size_t rows, void *dst)
+{
+    const size_t chunk = h->D.stage_bytes / width;
+    for (size_t r0 = 0; r0 < rows; r0 += chunk) {
+        const size_t n = (rows - r0 < chunk) ? rows - r0 : chunk;
+        CK(cudaMemcpyAsync(h->D.stage, (const char *)host_src + r0 * width, n * width, cudaMemcpyHostToDevice,
+                           h->stream));
+        CK(launch_rows_from_dense(h->D.stage, pitch, width, (int64_t)n, (char *)dst + r0 * pitch, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+    }
+    return OTM_OK;
+}
+
 extern "C" int otm_state(otm_handle *h, int32_t field, void *host_dst, size_t bytes)
 {
     if (!h || !host_dst) return OTM_ERR_ARG;
@@ -511,11 +543,12 @@ extern "C" int otm_state(otm_handle *h, int32_t field, void *host_dst, size_t by
     if (!field_view(h, field, &v)) return OTM_ERR_ARG;
     if (bytes != v.width * v.rows) return OTM_ERR_ARG;
     if (v.rows == 0) return OTM_OK;
-    if (v.pitch == v.width)
+    if (v.pitch == v.width) {
         CK(cudaMemcpyAsync(host_dst, v.src, bytes, cudaMemcpyDeviceToHost, h->stream));
-    else
-        CK(cudaMemcpy2DAsync(host_dst, v.width, v.src, v.pitch, v.width, v.rows, cudaMemcpyDeviceToHost,
-                             h->stream));
+    } else {   // pitched rows: packed on the device in chunks, each chunk one contiguous copy
+        const int rc = rows_d2h(h, v.src, v.pitch, v.width, v.rows, host_dst);
+        if (rc != OTM_OK) return rc;
+    }
     CK(cudaStreamSynchronize(h->stream));
     if (field == OTM_FIELD_SUPPORT_IDS || field == OTM_FIELD_SHAPE) {
         // rows are stored in linked-cell order; the export orders each row by node ID
@@ -595,11 +628,12 @@ extern "C" int otm_set_state(otm_handle *h, int32_t field, const void *host_src,
     FieldView v;
     field_view(h, field, &v);
     if (bytes != v.width * v.rows) return OTM_ERR_ARG;
-    if (v.pitch == v.width)
+    if (v.pitch == v.width) {
         CK(cudaMemcpyAsync((void *)v.src, host_src, bytes, cudaMemcpyHostToDevice, h->stream));
-    else
-        CK(cudaMemcpy2DAsync((void *)v.src, v.pitch, host_src, v.width, v.width, v.rows, cudaMemcpyHostToDevice,
-                             h->stream));
+    } else {
+        const int rc = rows_h2d(h, host_src, v.pitch, v.width, v.rows, (void *)v.src);
+        if (rc != OTM_OK) return rc;
+    }
     if (field == OTM_FIELD_NODE_DU)   // keep the FP32 copy of the increments in step
         CK(launch_du_to_f32(h->D, h->stream, &h->launches));
     CK(cudaStreamSynchronize(h->stream));
@@ -815,7 +849,8 @@ extern "C" int otm_adjoint_begin(otm_handle *h, void *adj_ws, size_t bytes, cons
     h->adj_swap = false;
     CK(cudaMemsetAsync(adj_ws, 0, need, h->stream));
     A = adj_view(h);
-    CK(cudaMemcpy2DAsync(A.xb, 32, xbar_host, 24, 24, (size_t)h->D.nn, cudaMemcpyHostToDevice, h->stream));
+    const int rc = rows_h2d(h, xbar_host, 32, 24, (size_t)h->D.nn, A.xb);
+    if (rc != OTM_OK) return rc;
     CK(cudaStreamSynchronize(h->stream));
     return OTM_OK;
 }
@@ -855,9 +890,11 @@ extern "C" int otm_adjoint_result(otm_handle *h, void *adj_ws, double *theta_bar
     const size_t nm = (size_t)h->D.nm;
     std::vector<double> th(5 * nm);
     CK(cudaMemcpyAsync(th.data(), A.thb, 5 * nm * 8, cudaMemcpyDeviceToHost, h->stream));
-    if (dubar_host)
-        CK(cudaMemcpy2DAsync(dubar_host, 24, A.dub, 32, 24, (size_t)h->D.nn, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
+    if (dubar_host) {
+        const int rc = rows_d2h(h, A.dub, 32, 24, (size_t)h->D.nn, dubar_host);
+        if (rc != OTM_OK) return rc;
+    }
     for (int k = 0; k < 5; k++) theta_bar[k] = 0.0;
     for (size_t p = 0; p < nm; p++)   // fixed order: deterministic
         for (int k = 0; k < 5; k++) theta_bar[k] += th[5 * p + k];

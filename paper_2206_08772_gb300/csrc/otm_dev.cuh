@@ -93,6 +93,8 @@ struct Dev {
     // status: (first offending id << 8) | (-code), atomicMin
     unsigned long long *err;
     int *emax;                       // largest binary exponent of the mass / force terms (2 ints)
+    char *stage;                     // staging for state transfers of pitched fields
+    size_t stage_bytes;
 };
 
 // scratch of the stand-alone support search (carved from caller memory)
@@ -294,6 +296,9 @@ cudaError_t launch_node_offsets(const Dev &D, int32_t *tmp, cudaStream_t s, long
 cudaError_t exp_table_setup();
 cudaError_t launch_exp_selftest(const double *x, int64_t n, double *mine, double *ref, cudaStream_t s);
 cudaError_t launch_node_update(const Dev &D, double t_next, cudaStream_t s, long long *launches);
+cudaError_t launch_rows_to_dense(const void *src, size_t pitch, size_t width, int64_t rows, void *dst, cudaStream_t s);
+cudaError_t launch_rows_from_dense(const void *src, size_t pitch, size_t width, int64_t rows, void *dst,
+                                   cudaStream_t s);
 cudaError_t launch_pack3to4(const double *x3, int64_t n, double4_32a *x4, cudaStream_t s, long long *launches);
 cudaError_t launch_init_state(const Dev &D, double T0, cudaStream_t s, long long *launches);
 cudaError_t launch_du_to_f32(const Dev &D, cudaStream_t s, long long *launches);

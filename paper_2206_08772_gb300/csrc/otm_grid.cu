@@ -396,6 +396,45 @@ __global__ void k_pack3to4(const double *__restrict__ x3, int64_t n, double4_32a
         x4[i] = make_double4_32a(x3[3 * i], x3[3 * i + 1], x3[3 * i + 2], 0.0);
 }
 
+// rows of `width` bytes (a multiple of 8) between a pitched layout and a dense one, 8 bytes per
+// thread: a state transfer then moves one contiguous block instead of many short rows
+__global__ void k_rows_to_dense(const char *__restrict__ src, size_t pitch, size_t width, int64_t rows,
+                                double *__restrict__ dst)
+{
+    const int64_t words = (int64_t)(width / 8), total = rows * words;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = t / words, w = t - r * words;
+        dst[t] = *(const double *)(src + (size_t)r * pitch + (size_t)w * 8);
+    }
+}
+
+__global__ void k_rows_from_dense(const double *__restrict__ src, size_t pitch, size_t width, int64_t rows,
+                                  char *__restrict__ dst)
+{
+    const int64_t words = (int64_t)(width / 8), total = rows * words;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = t / words, w = t - r * words;
+        *(double *)(dst + (size_t)r * pitch + (size_t)w * 8) = src[t];
+    }
+}
+
+cudaError_t launch_rows_to_dense(const void *src, size_t pitch, size_t width, int64_t rows, void *dst, cudaStream_t s)
+{
+    if (rows <= 0) return cudaSuccess;
+    k_rows_to_dense<<<grid_blocks(rows * (int64_t)(width / 8), 256), 256, 0, s>>>((const char *)src, pitch, width,
+                                                                                  rows, (double *)dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rows_from_dense(const void *src, size_t pitch, size_t width, int64_t rows, void *dst,
+                                   cudaStream_t s)
+{
+    if (rows <= 0) return cudaSuccess;
+    k_rows_from_dense<<<grid_blocks(rows * (int64_t)(width / 8), 256), 256, 0, s>>>((const double *)src, pitch,
+                                                                                    width, rows, (char *)dst);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_pack3to4(const double *x3, int64_t n, double4_32a *x4, cudaStream_t s, long long *launches)
 {
     if (n <= 0) return cudaSuccess;

@@ -264,3 +264,59 @@ def test_chip_deep_tool_embedding_inserts_nodes(orc, OTM):
     errs, bad = compare(sim_g, sim_o, {"default": 1e-10})
     print("chip insertion", errs)
     assert not bad, bad
+
+
+@pytest.mark.parametrize("host", [False, True])
+def test_snapshot_restore_continues_bit_exactly(OTM, host):
+    """Checkpoint / resume: a snapshot (device or page-locked host memory) taken at step 12 and
+    loaded back reproduces the uninterrupted run bit for bit, including the time-extrapolated
+    LME start (the previous lambda is part of the state)."""
+    p = scenarios.taylor_rod(h=0.8e-3, R=3.2e-3, L=9.6e-3, material=scenarios.copper_jc(), v0=400.0)
+    a = OTM(p)
+    assert a.step(12) == 0
+    snap = a.snapshot(host=host)
+    assert a.step(10) == 0
+    ref = {f: a.get(f) for f in FIELDS_NODE + FIELDS_MP}
+    b = OTM(p)
+    b.restore(snap)
+    assert b.step(10) == 0
+    for f in FIELDS_NODE + FIELDS_MP:
+        assert np.array_equal(b.get(f), ref[f]), f
+
+
+def test_snapshot_loads_across_precisions(orc, OTM):
+    """A snapshot of the FP64 path loads into a mixed-path handle (the FP32 increments are rebuilt
+    from the FP64 ones): the restored state equals the saved one, and the mixed path continues
+    within its stated error of the FP64 oracle."""
+    p = scenarios.taylor_rod(h=0.8e-3, R=3.2e-3, L=9.6e-3, material=scenarios.copper_jc())
+    a = OTM(p, precision="fp64")
+    assert a.step(10) == 0
+    snap = a.snapshot()
+    m = OTM(p, precision="mixed")
+    m.restore(snap)
+    for f in ("node_x", "node_du", "mp_x", "F", "sigma", "lam"):
+        assert np.array_equal(m.get(f), a.get(f)), f
+    assert m.step(10) == 0
+    o = orc.Sim(p)
+    assert o.step(20) == 0
+    assert rel(m.get("node_x"), o.get("node_x")) <= 1e-8
+    assert rel(m.get("sigma"), o.get("sigma")) <= 1e-3
+
+
+def test_pitched_state_transfer_round_trip(OTM):
+    """otm_state / otm_set_state of the fields stored with padding (node x, du, mass, force, MP x)
+    move exact bytes in both directions."""
+    p = scenarios.taylor_rod(h=0.8e-3, R=3.2e-3, L=9.6e-3, material=scenarios.copper_jc())
+    s = OTM(p)
+    assert s.step(3) == 0
+    rng = np.random.default_rng(4)
+    for f in ("node_x", "node_du", "mp_x"):
+        v = s.get(f)
+        w = v + rng.standard_normal(v.shape) * 1e-9
+        s.set(f, w)
+        assert np.array_equal(s.get(f), w), f
+        s.set(f, v)
+        assert np.array_equal(s.get(f), v), f
+    m, fr = s.get("node_mass"), s.get("node_force")
+    assert m.shape == (p.n_nodes,) and fr.shape == (p.n_nodes, 3)
+    assert abs(m.sum() - p.mp_mass.sum()) <= 1e-12 * p.mp_mass.sum()
