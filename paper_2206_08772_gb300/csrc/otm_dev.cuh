@@ -222,6 +222,42 @@ __device__ __forceinline__ double warp_reduce_scatter12(const double (&v)[12], i
     return d + __shfl_xor_sync(0xffffffffu, d, 1);
 }
 
+// Reduce-scatter of 10 per-lane values in 12 additions per lane. Afterwards lane L holds the
+// warp total of value rs10_value(L); rs10_writer(L) picks one lane per value, and value j can
+// be read from lane {0, 2, 4, 8, 10, 16, 18, 20, 24, 26}[j].
+__device__ __forceinline__ double warp_reduce_scatter10(const double (&v)[10], int lane)
+{
+    double a[5];
+#pragma unroll
+    for (int i = 0; i < 5; i++) {
+        const bool up = lane & 16;
+        const double mine = up ? v[5 + i] : v[i], other = up ? v[i] : v[5 + i];
+        a[i] = mine + __shfl_xor_sync(0xffffffffu, other, 16);
+    }
+    const bool up8 = lane & 8;
+    const double b0 = (up8 ? a[3] : a[0]) + __shfl_xor_sync(0xffffffffu, up8 ? a[0] : a[3], 8);
+    const double b1 = (up8 ? a[4] : a[1]) + __shfl_xor_sync(0xffffffffu, up8 ? a[1] : a[4], 8);
+    const double b2 = a[2] + __shfl_xor_sync(0xffffffffu, a[2], 8);
+    const bool up4 = lane & 4;
+    const double c0 = (up4 ? b2 : b0) + __shfl_xor_sync(0xffffffffu, up4 ? b0 : b2, 4);
+    const double c1 = b1 + __shfl_xor_sync(0xffffffffu, b1, 4);
+    const bool up2 = lane & 2;
+    const double dd = (up2 ? c1 : c0) + __shfl_xor_sync(0xffffffffu, up2 ? c0 : c1, 2);
+    return dd + __shfl_xor_sync(0xffffffffu, dd, 1);
+}
+
+__device__ __forceinline__ int rs10_value(int lane)
+{
+    const int base = (lane & 16) ? 5 : 0;
+    if (lane & 2) return base + ((lane & 8) ? 4 : 1);
+    return (lane & 4) ? base + 2 : base + ((lane & 8) ? 3 : 0);
+}
+
+__device__ __forceinline__ bool rs10_writer(int lane)
+{
+    return (lane & 1) == 0 && (lane & 14) != 12 && (lane & 6) != 6;
+}
+
 __device__ __forceinline__ int rs12_value(int lane)
 {
     return ((lane & 16) ? 6 : 0) + ((lane & 8) ? 3 : 0) + ((lane & 2) ? 1 : ((lane & 4) ? 2 : 0));

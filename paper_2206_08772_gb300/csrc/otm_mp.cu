@@ -170,10 +170,12 @@ __device__ __forceinline__ void lme_sums_safe(const double *dx, const double *dy
 
 __device__ __forceinline__ double rn2(const LmeSums &E) { return E.r0 * E.r0 + E.r1 * E.r1 + E.r2 * E.r2; }
 
-// J' = A - r r^T / Z and its adjugate / determinant (cofactors); false if not positive definite
-__device__ __forceinline__ bool lme_jinv(const LmeSums &E, double inv[6])
+// J' = A - r r^T / Z and its adjugate / determinant (cofactors); false if not positive definite.
+// iZ_out (optional) receives 1 / Z.
+__device__ __forceinline__ bool lme_jinv(const LmeSums &E, double inv[6], double *iZ_out = nullptr)
 {
     const double iZ = 1.0 / E.Z;
+    if (iZ_out) *iZ_out = iZ;
     const double s0 = E.r0 * iZ, s1 = E.r1 * iZ, s2 = E.r2 * iZ;
     const double j00 = E.a00 - s0 * E.r0, j11 = E.a11 - s1 * E.r1, j22 = E.a22 - s2 * E.r2;
     const double j01 = E.a01 - s0 * E.r1, j12 = E.a12 - s1 * E.r2, j02 = E.a02 - s0 * E.r2;
@@ -399,8 +401,64 @@ struct MpNewton {
     double t;          // step fraction of the pending trial
     double inv[6];     // J'^-1 at the solution (xx, yy, zz, xy, yz, xz)
     double iZ, logz;
+    double ts[3];      // the trial times 1024/ln2 (the exponent units of exp_scaled)
+    double sh;         // exponent shift of the pending evaluation
+    double qs;         // (solve's first shift - sh) * 1024/ln2, added to the stored prior terms
+    double shift0;     // the solve's first shift (the stored prior terms are relative to it)
     int state, have_cur, iters, iters_total, halvings, retried;
 };
+
+// the scaled trial and the shift of the pending evaluation: trials share the current point's
+// shift, the first evaluation of a start uses the solve's first shift
+__device__ __forceinline__ void newton_set_trial(MpNewton &m)
+{
+    m.sh = m.have_cur ? m.C[10] : m.shift0;
+    m.qs = (m.shift0 - m.sh) * kExpScale;
+    for (int i = 0; i < 3; i++) m.ts[i] = m.trial[i] * kExpScale;
+}
+
+// One evaluation of the block path (Eq. 14 sums at the pending trial of MP state m): weights
+// into W.w, the sums into m.E (written by one lane per value), m.E[10] = the shift used. If Z
+// over- or underflows, again with the shift at the largest exponent. Warp-uniform.
+template <bool SHIFTED>
+__device__ __forceinline__ void lme_acc10(const WarpSmem &W, int n, double s0, double s1, double s2, double qs,
+                                          int lane, const double *T, double (&v)[10])
+{
+#pragma unroll
+    for (int i = 0; i < 10; i++) v[i] = 0.0;
+    for (int k = lane; k < n; k += kWarp) {
+        const double x = W.dx[k], y = W.dy[k], z = W.dz[k];
+        const double qk = SHIFTED ? W.q[k] + qs : W.q[k];
+        const double wk = exp_scaled(fma(s2, z, fma(s1, y, fma(s0, x, qk))), T);
+        W.w[k] = wk;
+        const double wx = wk * x, wy = wk * y, wz = wk * z;
+        v[0] += wk;
+        v[1] += wx; v[2] += wy; v[3] += wz;
+        v[4] = fma(wx, x, v[4]); v[5] = fma(wy, y, v[5]); v[6] = fma(wz, z, v[6]);
+        v[7] = fma(wx, y, v[7]); v[8] = fma(wy, z, v[8]); v[9] = fma(wx, z, v[9]);
+    }
+}
+
+__device__ void lme_eval_block(const WarpSmem &W, int n, MpNewton &m, int lane, const double *T)
+{
+    const double s0 = m.ts[0], s1 = m.ts[1], s2 = m.ts[2];
+    double qs = m.qs, sh = m.sh;
+    double v[10];
+    if (qs == 0.0) lme_acc10<false>(W, n, s0, s1, s2, qs, lane, T, v);
+    else lme_acc10<true>(W, n, s0, s1, s2, qs, lane, T, v);
+    double t = warp_reduce_scatter10(v, lane);
+    const double Z = __shfl_sync(0xffffffffu, t, 0);
+    if (!(Z > 1e-200) || !(Z < 1e200)) {
+        double mx = -INFINITY;
+        for (int k = lane; k < n; k += kWarp) mx = fmax(mx, W.q[k] + (s0 * W.dx[k] + s1 * W.dy[k] + s2 * W.dz[k]));
+        sh = warp_max(mx) * (1.0 / kExpScale) + m.shift0;
+        qs = (m.shift0 - sh) * kExpScale;
+        lme_acc10<true>(W, n, s0, s1, s2, qs, lane, T, v);
+        t = warp_reduce_scatter10(v, lane);
+    }
+    if (rs10_writer(lane)) m.E[rs10_value(lane)] = t;
+    if (lane == 0) m.E[10] = sh;
+}
 
 __device__ __forceinline__ LmeSums sums_of(const double *v)
 {
@@ -421,6 +479,7 @@ __device__ __forceinline__ void newton_fail(MpNewton &m)
         m.halvings = 0;
         m.ws[0] = m.ws[1] = m.ws[2] = 0.0;
         m.trial[0] = m.trial[1] = m.trial[2] = 0.0;
+        newton_set_trial(m);
         m.state = kNewtonEval;
     } else {
         m.state = kNewtonFail;
@@ -448,6 +507,7 @@ __device__ void newton_round(MpNewton &m, double tol, int max_it)
             }
             m.t *= 0.5;
             for (int i = 0; i < 3; i++) m.trial[i] = fma(m.t, m.dir[i], m.lam[i]);
+            newton_set_trial(m);
             return;
         }
     }
@@ -458,14 +518,16 @@ __device__ void newton_round(MpNewton &m, double tol, int max_it)
         return;
     }
     double inv[6];
-    if (r2 <= tol * tol * c.Z * c.Z) {   // converged: J'^-1, 1/Z and log Z for the outputs
-        if (!lme_jinv(c, inv)) {
+    if (r2 <= tol * tol * c.Z * c.Z) {   // converged: J'^-1, 1/Z and the next shift for the outputs
+        if (!lme_jinv(c, inv, &m.iZ)) {
             newton_fail(m);
             return;
         }
         for (int i = 0; i < 6; i++) m.inv[i] = inv[i];
-        m.iZ = 1.0 / c.Z;
-        m.logz = c.shift + log(c.Z);
+        // the next solve's shift only has to keep the weights near 1: log Z to within ln 2,
+        // from the binary exponent of Z (Z > 0 and finite here)
+        const int ez = ((__double2hiint(c.Z) >> 20) & 0x7ff) - 1023;
+        m.logz = fma((double)ez, 0x1.62e42fefa39efp-1, c.shift);
         m.state = kNewtonDone;
         return;
     }
@@ -480,6 +542,7 @@ __device__ void newton_round(MpNewton &m, double tol, int max_it)
     m.dir[2] = -(inv[5] * c.r0 + inv[4] * c.r1 + inv[2] * c.r2);
     m.t = 1.0;
     for (int i = 0; i < 3; i++) m.trial[i] = fma(m.t, m.dir[i], m.lam[i]);
+    newton_set_trial(m);
 }
 
 size_t lme_smem_bytes(int S, int warps)
@@ -673,6 +736,8 @@ __global__ void __launch_bounds__(kLmeWarps * kWarp) k_lme(const Dev D)
             M.trial[2] = M.ws[2] = l2;
             M.t = 1.0;
             M.have_cur = M.iters = M.iters_total = M.halvings = M.retried = 0;
+            M.shift0 = shift0;
+            newton_set_trial(M);
             M.state = cnt > 0 ? kNewtonEval : kNewtonFail;
         }
     } else if (lane == 0) {
@@ -683,16 +748,7 @@ __global__ void __launch_bounds__(kLmeWarps * kWarp) k_lme(const Dev D)
     for (;;) {
         if (M.state == kNewtonEval) {
             __syncwarp();
-            LmeSums E;
-            // trials share the current point's exponent shift (the first one: the solve's shift)
-            const double sh = M.have_cur ? M.C[10] : shift0;
-            lme_sums_safe(W.dx, W.dy, W.dz, W.q, W.w, cnt, M.trial[0], M.trial[1], M.trial[2], sh, shift0, lane, T,
-                          E);
-            __syncwarp();
-            if (lane == 0) {
-                const double s11[11] = {E.Z, E.r0, E.r1, E.r2, E.a00, E.a11, E.a22, E.a01, E.a12, E.a02, E.shift};
-                for (int i = 0; i < 11; i++) M.E[i] = s11[i];
-            }
+            lme_eval_block(W, cnt, M, lane, T);
         }
         __syncthreads();
         bool pending = false;
