@@ -226,6 +226,7 @@ def time_e2e(prob, precision, steps, torch, host_snap):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     sim.restore(host_snap)
+    t_restore = time.perf_counter() - t0
     for _ in range(steps):
         st = sim.step(1, sync=False)
         if st != 0:
@@ -235,7 +236,7 @@ def time_e2e(prob, precision, steps, torch, host_snap):
     t = time.perf_counter() - t0
     sim.close()
     return dict(value=prob.n_mps * steps / t, unit=UNIT, h2d_bytes_per_step=int(h2d // max(steps, 1)),
-                d2h_bytes_per_step=int(out.nbytes), seconds=t)
+                d2h_bytes_per_step=int(out.nbytes), seconds=t, restore_seconds=t_restore)
 
 
 def time_adjoint(steps: int, torch):

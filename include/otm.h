@@ -211,9 +211,13 @@ int otm_adjoint_bytes(otm_handle *h, size_t *bytes);
  * d objective / d node positions; every other adjoint starts at zero. */
 int otm_adjoint_begin(otm_handle *h, void *adj_ws, size_t bytes, const double *xbar_host);
 /* One backward step. Precondition: the handle holds state n (e.g. from otm_snapshot_load) and
- * the adjoint workspace holds the adjoint of state n+1. The call recomputes step n (which is
- * deterministic), then propagates the adjoint to state n. The handle then holds state n+1. */
-int otm_adjoint_step(otm_handle *h, void *adj_ws);
+ * the adjoint workspace holds the adjoint of state n+1. The call needs state n+1 and the node
+ * masses and forces of step n: with next_snapshot NULL it recomputes step n (deterministic);
+ * with next_snapshot a snapshot of state n+1 (device or page-locked host memory, as written by
+ * otm_snapshot_save on this trajectory) it runs only the node update of step n and loads state
+ * n+1, which is cheaper (no search, return map or Newton solve). Then it propagates the adjoint
+ * to state n. The handle then holds state n+1. */
+int otm_adjoint_step(otm_handle *h, void *adj_ws, const void *next_snapshot);
 /* theta_bar[5] = d objective / d (A, B, n, C, m); dubar_host (n_nodes x 3, optional) =
  * d objective / d (displacement increments of the state the backward pass has reached). */
 int otm_adjoint_result(otm_handle *h, void *adj_ws, double *theta_bar, double *dubar_host);

@@ -95,7 +95,7 @@ _SIGS = {
     "otm_snapshot_load": (C.c_int, [_P, _P]),
     "otm_adjoint_bytes": (C.c_int, [_P, _P]),
     "otm_adjoint_begin": (C.c_int, [_P, _P, _SZ, _P]),
-    "otm_adjoint_step": (C.c_int, [_P, _P]),
+    "otm_adjoint_step": (C.c_int, [_P, _P, _P]),
     "otm_adjoint_result": (C.c_int, [_P, _P, _P, _P]),
 }
 

@@ -80,9 +80,10 @@ def backward_pass(sim: OTM, prob, steps: int, every: int, checkpoints: dict, fin
             if sim.step(1) != 0:
                 raise RuntimeError("recompute failed")
             states.append(sim.snapshot())
+        end = checkpoints[s1] if s1 in checkpoints else final    # state s1
         for k in range(s1 - 1, s0 - 1, -1):
             sim.restore(states[k - s0])
-            sim.adjoint_step()
+            sim.adjoint_step(states[k + 1 - s0] if k + 1 - s0 < len(states) else end)
         del states
     thb, dub = sim.adjoint_result()
     out = np.zeros(6)

@@ -855,7 +855,7 @@ extern "C" int otm_adjoint_begin(otm_handle *h, void *adj_ws, size_t bytes, cons
     return OTM_OK;
 }
 
-extern "C" int otm_adjoint_step(otm_handle *h, void *adj_ws)
+extern "C" int otm_adjoint_step(otm_handle *h, void *adj_ws, const void *next_snapshot)
 {
     if (!h || !adj_ws || adj_ws != h->adj_ws) return OTM_ERR_ARG;
     AdjDev A = adj_view(h);
@@ -875,9 +875,20 @@ extern "C" int otm_adjoint_step(otm_handle *h, void *adj_ws)
     CK(cudaMemcpyAsync(A.cnt_n, D.cnt, 4 * nm, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(A.rank_n, D.rank, 2 * slots, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(A.noff_n, D.noff, 4 * (nn + 1), cudaMemcpyDeviceToDevice, s));
-    // step n again (deterministic: reproduces the trajectory), then back-propagate through it
-    int rc = enqueue_step(h);
-    if (rc != OTM_OK) return rc;
+    if (next_snapshot) {
+        // the node update of step n (its masses and forces feed the node adjoint), then state
+        // n+1 from its snapshot (the update's positions and increments are the snapshot's)
+        {
+            PhaseScope ps(h, OTM_PHASE_NODE_UPDATE);
+            CK(launch_node_update(D, (double)(h->step + 1) * D.dt, s, &h->launches));
+        }
+        const int rc = otm_snapshot_load(h, next_snapshot);
+        if (rc != OTM_OK) return rc;
+    } else {
+        // step n again (deterministic: reproduces the trajectory)
+        const int rc = enqueue_step(h);
+        if (rc != OTM_OK) return rc;
+    }
     CK(launch_adjoint_backward(D, A, s, &h->launches));
     h->adj_swap = !h->adj_swap;   // the adjoint of shape n becomes the current pair adjoint
     return read_error(h, nullptr, nullptr);

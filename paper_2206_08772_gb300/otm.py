@@ -168,8 +168,10 @@ class OTM:
         xb = np.ascontiguousarray(xbar, dtype=np.float64)
         check(L.otm_adjoint_begin(self._h, C.c_void_p(self._adj_ptr), nb.value, _ptr(xb)), "otm_adjoint_begin")
 
-    def adjoint_step(self):
-        check(_lib.load().otm_adjoint_step(self._h, C.c_void_p(self._adj_ptr)), "otm_adjoint_step")
+    def adjoint_step(self, next_snapshot=None):
+        """One backward step from state n (held); next_snapshot (optional) holds state n+1."""
+        nxt = C.c_void_p(next_snapshot[1]) if next_snapshot is not None else C.c_void_p(0)
+        check(_lib.load().otm_adjoint_step(self._h, C.c_void_p(self._adj_ptr), nxt), "otm_adjoint_step")
 
     def adjoint_result(self):
         thb = np.zeros(5)
