@@ -209,18 +209,17 @@ def phase_profile(sim, steps: int = 3):
     return {k: (ms / n if n else 0.0) for k, (ms, n) in pt.items()}
 
 
-def time_e2e(prob, precision, steps, torch, host_snap):
-    """Through the C ABI from page-locked host memory: the state at the start of the timed window
-    is loaded from a host snapshot (H2D of every node, MP and support array, then the shape
-    functions regenerated), then per step otm_step + a D2H read of the node positions."""
-    from paper_2206_08772_gb300.otm import OTM
+def time_e2e(sim, prob, steps, torch, host_snap):
+    """Through the C ABI from page-locked host memory, on an existing handle of the problem: the
+    state at the start of the timed window is loaded from a host snapshot (H2D of every node, MP
+    and support array, then the shape functions regenerated), then per step otm_step + a D2H
+    read of the node positions."""
 
     def pinned(a):
         t = torch.empty(a.shape, dtype=getattr(torch, str(a.dtype)), pin_memory=True)
         t.numpy()[...] = a
         return t.numpy()
 
-    sim = OTM(prob, precision=precision)
     out = pinned(np.zeros((prob.n_nodes, 3)))
     h2d = host_snap[0].numel()
     torch.cuda.synchronize()
@@ -234,7 +233,6 @@ def time_e2e(prob, precision, steps, torch, host_snap):
         sim.get("node_x", out=out)
     torch.cuda.synchronize()
     t = time.perf_counter() - t0
-    sim.close()
     return dict(value=prob.n_mps * steps / t, unit=UNIT, h2d_bytes_per_step=int(h2d // max(steps, 1)),
                 d2h_bytes_per_step=int(out.nbytes), seconds=t, restore_seconds=t_restore)
 
@@ -406,9 +404,6 @@ def main():
                              save_snaps=True)
     snap_dev, snap_host = info.pop("snaps")
     phases = phase_profile(sim)
-    sim.close()
-    del sim
-    torch.cuda.empty_cache()
     ms, value = aggregate(info["ms"], prob.n_mps, args.steps, world, dist, device="cuda")
 
     mixed = None
@@ -428,8 +423,11 @@ def main():
         torch.cuda.empty_cache()
     e2e = None
     if not args.no_e2e:
-        e2e = time_e2e(prob, "fp64", args.steps, torch, snap_host)
+        e2e = time_e2e(sim, prob, args.steps, torch, snap_host)
         e2e["value"] *= world
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()

@@ -161,6 +161,20 @@ int otm_set_state(otm_handle *h, int32_t field, const void *host_src, size_t byt
 /* Rebuild supports, shape functions and node-major lists from the current positions. */
 int otm_refresh(otm_handle *h);
 
+/* Topology freezing, for finite-difference checks of the adjoint (which holds the supports of
+ * the differentiated trajectory fixed). With on != 0 the following steps skip the support
+ * search: every step keeps the supports it starts with, and the LME solve (Eq. 14) runs at the
+ * new positions over them. OTM_ERR_ARG for problems that erode MPs or insert nodes. */
+int otm_freeze_topology(otm_handle *h, int32_t on);
+
+/* One step (as otm_step) whose new supports are given instead of searched, so that a perturbed
+ * run can replay the supports recorded from a base run step by step: counts (host, n_mps int32,
+ * each 1..max_support) and ids (host, n_mps rows of max_support int32; row p holds counts[p]
+ * node indices in [0, n_nodes), any order, the rest is ignored). OTM_ERR_ARG on a bad count or
+ * index (nothing runs), OTM_ERR_CAPACITY if a node gets more than 65,535 influences; not for
+ * problems that erode MPs or insert nodes. Synchronises. */
+int otm_step_with_supports(otm_handle *h, const int32_t *counts, const int32_t *ids);
+
 /* First error recorded on the device: its code and the smallest offending ID. Synchronises. */
 int otm_error_detail(otm_handle *h, int32_t *code, int64_t *first_id);
 

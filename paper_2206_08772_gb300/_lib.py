@@ -96,6 +96,8 @@ _SIGS = {
     "otm_adjoint_bytes": (C.c_int, [_P, _P]),
     "otm_adjoint_begin": (C.c_int, [_P, _P, _SZ, _P]),
     "otm_adjoint_step": (C.c_int, [_P, _P, _P]),
+    "otm_freeze_topology": (C.c_int, [_P, C.c_int32]),
+    "otm_step_with_supports": (C.c_int, [_P, _P, _P]),
     "otm_adjoint_result": (C.c_int, [_P, _P, _P, _P]),
 }
 

@@ -542,7 +542,9 @@ __global__ void k_rebuild_ranks(const Dev D)
         const int64_t p = t / D.S;
         const int k = (int)(t - p * D.S);
         if (k >= D.cnt[p]) continue;
-        D.rank[t] = (uint16_t)atomicAdd(&D.ncount[D.ids[t]], 1);
+        const int r = atomicAdd(&D.ncount[D.ids[t]], 1);
+        if (r > 0xffff) raise_error(D.err, OTM_ERR_CAPACITY, D.ngid[D.ids[t]]);
+        D.rank[t] = (uint16_t)r;
     }
 }
 

@@ -25,6 +25,7 @@ struct otm_handle {
     int64_t n_eroded, n_removed, n_inserted;
     int64_t nn0, nm0;              // sizes at initialisation
     int64_t nn_cap;                // node array capacity (nn0 + max_insert)
+    bool frozen;                   // topology frozen: steps keep their supports
     // adjoint
     void *adj_ws;
     bool adj_swap;
@@ -359,6 +360,26 @@ static int enqueue_step(otm_handle *h)
         PhaseScope ps(h, OTM_PHASE_NODE_UPDATE);
         CK(launch_node_update(D, t_next, s, &h->launches));
     }
+    if (h->frozen) {
+        // frozen topology: kinematics (3) and return map (4) over the supports the step starts
+        // with, then the LME (6) at the new positions over the same supports and lists
+        {
+            PhaseScope ps(h, OTM_PHASE_KINEMATICS);
+            CK(launch_kinematics(D, s, &h->launches));
+        }
+        {
+            PhaseScope ps(h, OTM_PHASE_RETURN_MAP);
+            CK(launch_return_map(D, s, &h->launches));
+        }
+        CK(cudaMemsetAsync(D.emax, 0x80, 2 * sizeof(int), s));
+        {
+            PhaseScope ps(h, OTM_PHASE_LME);
+            D.lme_mode = kLmeStep;
+            CK(launch_lme(D, s, &h->launches));
+        }
+        h->step++;
+        return OTM_OK;
+    }
     if (!D.allow_erode) {
         // no MP can leave the body within the step: the kinematics gather (3) and the search at
         // the new MP position (5) run in one kernel, then the return map (4) and the LME (6)
@@ -646,6 +667,59 @@ extern "C" int otm_refresh(otm_handle *h)
     CK(cudaMemsetAsync(h->D.err, 0xff, sizeof(unsigned long long), h->stream));
     int rc = rebuild_supports(h, false, kLmePlain);
     if (rc != OTM_OK) return rc;
+    return read_error(h, nullptr, nullptr);
+}
+
+extern "C" int otm_freeze_topology(otm_handle *h, int32_t on)
+{
+    if (!h) return OTM_ERR_ARG;
+    if (on && (h->P.allow_erode || h->P.max_insert > 0)) return OTM_ERR_ARG;
+    h->frozen = on != 0;
+    return OTM_OK;
+}
+
+extern "C" int otm_step_with_supports(otm_handle *h, const int32_t *counts, const int32_t *ids)
+{
+    if (!h || !counts || !ids) return OTM_ERR_ARG;
+    if (h->P.allow_erode || h->P.max_insert > 0) return OTM_ERR_ARG;
+    Dev &D = h->D;
+    const int64_t nm = D.nm, S = D.S, nn = D.nn;
+    for (int64_t p = 0; p < nm; p++) {
+        if (counts[p] < 1 || counts[p] > S) return OTM_ERR_ARG;
+        const int32_t *row = ids + p * S;
+        for (int32_t k = 0; k < counts[p]; k++)
+            if (row[k] < 0 || row[k] >= nn) return OTM_ERR_ARG;
+    }
+    cudaStream_t s = h->stream;
+    const double t_next = (double)(h->step + 1) * D.dt;
+    {
+        PhaseScope ps(h, OTM_PHASE_NODE_UPDATE);
+        CK(launch_node_update(D, t_next, s, &h->launches));
+    }
+    {   // kinematics over the supports of the state the step starts from
+        PhaseScope ps(h, OTM_PHASE_KINEMATICS);
+        CK(launch_kinematics(D, s, &h->launches));
+    }
+    {
+        PhaseScope ps(h, OTM_PHASE_RETURN_MAP);
+        CK(launch_return_map(D, s, &h->launches));
+    }
+    // the given supports of the new state (stream-ordered after the kinematics read the old ones)
+    CK(cudaMemcpyAsync(D.cnt, counts, (size_t)nm * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(D.ids, ids, (size_t)(nm * S) * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(D.ncount, 0, (size_t)nn * sizeof(int32_t), s));
+    CK(cudaMemsetAsync(D.emax, 0x80, 2 * sizeof(int), s));
+    CK(launch_rebuild_ranks(D, s, &h->launches));
+    {
+        PhaseScope ps(h, OTM_PHASE_NODE_MAJOR);
+        CK(launch_node_offsets(D, h->scan_tmp, s, &h->launches));
+    }
+    {
+        PhaseScope ps(h, OTM_PHASE_LME);
+        D.lme_mode = kLmeStep;
+        CK(launch_lme(D, s, &h->launches));
+    }
+    h->step++;
     return read_error(h, nullptr, nullptr);
 }
 

@@ -168,6 +168,18 @@ class OTM:
         xb = np.ascontiguousarray(xbar, dtype=np.float64)
         check(L.otm_adjoint_begin(self._h, C.c_void_p(self._adj_ptr), nb.value, _ptr(xb)), "otm_adjoint_begin")
 
+    def freeze_topology(self, on: bool = True):
+        """Skip the support search in the following steps (see otm_freeze_topology)."""
+        check(_lib.load().otm_freeze_topology(self._h, int(on)), "otm_freeze_topology")
+
+    def step_with_supports(self, counts: np.ndarray, ids: np.ndarray) -> int:
+        """One step whose new supports are given: counts (n_mps,), ids (n_mps, max_support)."""
+        c = np.ascontiguousarray(counts, dtype=np.int32)
+        i = np.ascontiguousarray(ids, dtype=np.int32)
+        if i.shape != (c.size, self.S):
+            raise ValueError("ids must be (n_mps, max_support)")
+        return _lib.load().otm_step_with_supports(self._h, _ptr(c), _ptr(i))
+
     def adjoint_step(self, next_snapshot=None):
         """One backward step from state n (held); next_snapshot (optional) holds state n+1."""
         nxt = C.c_void_p(next_snapshot[1]) if next_snapshot is not None else C.c_void_p(0)

@@ -57,3 +57,36 @@ def test_gpu_adjoint_matches_finite_differences():
         fd = (f[0] - f[1]) / (2 * h)
         noise = 20 * np.finfo(float).eps * abs(L.item()) / h
         assert abs(fd - gL[k].item()) <= 1e-6 * abs(gL[k].item()) + noise, (k, fd, gL[k].item())
+
+
+def test_gpu_adjoint_against_finite_differences_with_replayed_supports():
+    """Central differences of the GPU forward with the base trajectory's supports replayed at
+    every step (otm_step_with_supports), so that no support change can enter the difference:
+    all six parameters, both objectives, against the GPU adjoint (1e-6 relative)."""
+    from paper_2206_08772_gb300.adjoint import objectives_and_seeds, rod_objectives
+    from paper_2206_08772_gb300.otm import OTM
+    steps = 10
+    th = torch.tensor(THETA0, dtype=torch.float64, requires_grad=True)
+    vals = rod_objectives(th, make_rod, steps)
+    grads = [torch.autograd.grad(vals[o], th, retain_graph=True)[0].numpy() for o in range(2)]
+    base = OTM(make_rod(THETA0))
+    rec = []
+    for _ in range(steps):
+        assert base.step(1) == 0
+        rec.append((base.get("support_count"), base.get("support_ids")))
+    _, _, (i_len, i_rad) = objectives_and_seeds(base.get("node_x"), base.get("node_mass"), 0.8e-3)
+    for k in range(6):
+        hk = 1e-6 * THETA0[k]
+        f = []
+        for sg in (1, -1):
+            t = THETA0.copy()
+            t[k] += sg * hk
+            s = OTM(make_rod(t))
+            for j in range(steps):
+                assert s.step_with_supports(*rec[j]) == 0
+            x = s.get("node_x")
+            f.append((x[i_len, 2], np.hypot(x[i_rad, 0], x[i_rad, 1])))
+        for o in range(2):
+            fd = (f[0][o] - f[1][o]) / (2 * hk)
+            noise = 20 * np.finfo(float).eps * abs(vals[o].item()) / hk
+            assert abs(fd - grads[o][k]) <= 1e-6 * abs(grads[o][k]) + noise, (k, o, fd, grads[o][k])

@@ -320,3 +320,37 @@ def test_pitched_state_transfer_round_trip(OTM):
     m, fr = s.get("node_mass"), s.get("node_force")
     assert m.shape == (p.n_nodes,) and fr.shape == (p.n_nodes, 3)
     assert abs(m.sum() - p.mp_mass.sum()) <= 1e-12 * p.mp_mass.sum()
+
+
+def test_replayed_supports_reproduce_the_base_run(OTM):
+    """otm_step_with_supports: a run that takes, at every step, the supports a base run found
+    (instead of searching) reproduces the base run; here the impact changes the supports, so
+    the replay is not trivially the frozen initial topology."""
+    p = scenarios.taylor_rod(h=0.8e-3, R=3.2e-3, L=9.6e-3, material=scenarios.copper_jc(), v0=400.0)
+    base = OTM(p)
+    first = base.get("support_ids")
+    rec = []
+    for _ in range(12):
+        assert base.step(1) == 0
+        rec.append((base.get("support_count"), base.get("support_ids")))
+    assert not np.array_equal(rec[-1][1], first)
+    rep = OTM(p)
+    for k in range(12):
+        assert rep.step_with_supports(*rec[k]) == 0, rep.error()
+        assert np.array_equal(rep.get("support_ids"), rec[k][1])
+    for f in FIELDS_NODE + FIELDS_MP:
+        assert rel(rep.get(f), base.get(f)) <= 1e-12, f
+
+
+def test_frozen_topology_keeps_the_supports(OTM):
+    p = scenarios.taylor_rod(h=0.8e-3, R=3.2e-3, L=9.6e-3, material=scenarios.copper_jc(), v0=400.0)
+    s = OTM(p)
+    ids0, cnt0 = s.get("support_ids"), s.get("support_count")
+    s.freeze_topology(True)
+    assert s.step(12) == 0
+    assert np.array_equal(s.get("support_ids"), ids0) and np.array_equal(s.get("support_count"), cnt0)
+    bad = np.full(ids0.shape, p.n_nodes + 5, np.int32)
+    assert s.step_with_supports(np.minimum(cnt0, 1), bad) == -1     # out-of-range index: refused
+    e = OTM(scenarios.chip_block(h=0.02e-3, size=(0.4e-3, 0.2e-3, 0.1e-3), depth=0.06e-3, steps=2))
+    with pytest.raises(Exception):
+        e.freeze_topology(True)                                      # eroding problem: refused
