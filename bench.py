@@ -155,7 +155,8 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------------- GPU arm
-def time_gpu(prob, precision, steps, warmup, torch, dist, start: int = 0, snap=None, save_snaps: bool = False):
+def time_gpu(prob, precision, steps, warmup, torch, dist, start: int = 0, snap=None, save_snaps: bool = False,
+             profile_window: bool = False):
     """K timed steps after W warm-up steps, from the state after `start` untimed steps (or from
     the snapshot `snap`). With save_snaps the state there is also returned as a device and a
     page-locked host snapshot."""
@@ -179,10 +180,15 @@ def time_gpu(prob, precision, steps, warmup, torch, dist, start: int = 0, snap=N
     torch.cuda.synchronize()
     l0 = sim.launches()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if profile_window:   # marks the timed steps for a profiler started with --profile-from-start off
+        import torch.cuda.profiler
+        torch.cuda.profiler.start()
     e0.record(stream)
     st = sim.step(steps, sync=False)
     e1.record(stream)
     torch.cuda.synchronize()
+    if profile_window:
+        torch.cuda.profiler.stop()
     if dist is not None:
         dist.barrier()
     ms = e0.elapsed_time(e1)
@@ -354,6 +360,8 @@ def main():
     ap.add_argument("--start-step", type=int, default=500,
                     help="untimed steps before the warm-up (the timed window sits mid-run)")
     ap.add_argument("--sweep", action="store_true", help="run the 16-rod mixed-precision sweep instead")
+    ap.add_argument("--profile-window", action="store_true",
+                    help="cudaProfilerStart/Stop around the timed FP64 steps (for ncu --profile-from-start off)")
     ap.add_argument("--sweep-steps", type=int, default=200)
     args = ap.parse_args()
 
@@ -401,7 +409,7 @@ def main():
 
     with ClockSampler(local) as clk:
         sim, info = time_gpu(prob, "fp64", args.steps, args.warmup, torch, dist, start=args.start_step,
-                             save_snaps=True)
+                             save_snaps=True, profile_window=args.profile_window)
     snap_dev, snap_host = info.pop("snaps")
     phases = phase_profile(sim)
     ms, value = aggregate(info["ms"], prob.n_mps, args.steps, world, dist, device="cuda")
