@@ -140,7 +140,9 @@ int otm_init(const otm_problem *prob, const otm_params *params, void *stream, vo
  * Both keep every array in ascending ID order (stream compaction, appended IDs). */
 int otm_step(otm_handle *h, int32_t n_steps);
 
-/* Same as otm_step but does not synchronise; errors are reported by otm_error_detail. */
+/* Same as otm_step but does not synchronise at the end; errors are reported by
+ * otm_error_detail. Problems that erode MPs or insert nodes still synchronise inside each step
+ * (the host reads how many entries leave or arrive before it sizes the following launches). */
 int otm_step_async(otm_handle *h, int32_t n_steps);
 
 /* Current sizes (host-side view; exact after otm_step returns). */
@@ -192,7 +194,7 @@ enum {
     OTM_PHASE_SEARCH = 4,        /* Algorithm 3 steps 2-3: supports, influence counts */
     OTM_PHASE_NODE_MAJOR = 5,    /* influence-list offsets (scan of the counts) */
     OTM_PHASE_LME = 6,           /* Eq. 14 + per-pair contributions in node-major order */
-    OTM_PHASE_COMPACT = 7,       /* erosion (Sec. 4.2 fracture) and orphan-node removal */
+    OTM_PHASE_COMPACT = 7,       /* erosion (Sec. 4.2 fracture), orphan-node removal, node insertion */
     OTM_N_PHASES = 8
 };
 int otm_phase_timing(otm_handle *h, int32_t enable);
