@@ -676,13 +676,14 @@ cudaError_t launch_search(const Dev &D, cudaStream_t s, long long *launches)
 __device__ __forceinline__ void lme_record(const Dev &D, int64_t p, double l0, double l1, double l2)
 {
     if (D.lme_mode == kLmeStep) {
-        D.lam_prev[3 * p] = D.lam[3 * p];
-        D.lam_prev[3 * p + 1] = D.lam[3 * p + 1];
-        D.lam_prev[3 * p + 2] = D.lam[3 * p + 2];
+        for (int i = 0; i < 3; i++) {
+            D.lam_prev2[3 * p + i] = D.lam_prev[3 * p + i];
+            D.lam_prev[3 * p + i] = D.lam[3 * p + i];
+        }
     } else if (D.lme_mode == kLmePlain) {
-        D.lam_prev[3 * p] = l0;
-        D.lam_prev[3 * p + 1] = l1;
-        D.lam_prev[3 * p + 2] = l2;
+        D.lam_prev[3 * p] = D.lam_prev2[3 * p] = l0;
+        D.lam_prev[3 * p + 1] = D.lam_prev2[3 * p + 1] = l1;
+        D.lam_prev[3 * p + 2] = D.lam_prev2[3 * p + 2] = l2;
     }
     D.lam[3 * p] = l0;
     D.lam[3 * p + 1] = l1;
@@ -722,14 +723,14 @@ __global__ void __launch_bounds__(kLmeWarps * kWarp) k_lme(const Dev D)
             W.q[k] = fma(-beta_s, fma(z, z, fma(y, y, x * x)), -shift_s);
         }
         if (lane == 0) {
-            // Eq. 14: the warm start is the previous step's lambda, or (within a step) its
-            // linear extrapolation in time, which leaves fewer Newton iterations while the
-            // material deforms smoothly
+            // Eq. 14: the warm start is the previous step's lambda, or (within a step) the
+            // quadratic through the last three solutions, 3 l_n - 3 l_{n-1} + l_{n-2}: while
+            // the material deforms smoothly one Newton step from it meets the tolerance
             double l0 = D.lam[3 * p], l1 = D.lam[3 * p + 1], l2 = D.lam[3 * p + 2];
             if (D.lme_mode == kLmeStep) {
-                l0 = 2.0 * l0 - D.lam_prev[3 * p];
-                l1 = 2.0 * l1 - D.lam_prev[3 * p + 1];
-                l2 = 2.0 * l2 - D.lam_prev[3 * p + 2];
+                l0 = fma(3.0, l0 - D.lam_prev[3 * p], D.lam_prev2[3 * p]);
+                l1 = fma(3.0, l1 - D.lam_prev[3 * p + 1], D.lam_prev2[3 * p + 1]);
+                l2 = fma(3.0, l2 - D.lam_prev[3 * p + 2], D.lam_prev2[3 * p + 2]);
             }
             M.trial[0] = M.ws[0] = l0;
             M.trial[1] = M.ws[1] = l1;

@@ -116,7 +116,7 @@ class Problem:
     gamma: float = 0.8
     support_tol: float = 1e-6
     T0: float = 298.0
-    newton_tol: float = 1e-13     # LME residual tolerance, relative to h
+    newton_tol: float = 1e-14     # LME residual tolerance, relative to h
     max_newton: int = 50
     eps_stab: float = 0.0
     max_insert: int = 0           # node slots for insertion over the run (0: insertion off)
