@@ -119,6 +119,7 @@ static size_t layout(int64_t nn, int64_t nn_cap, int64_t nm, int S, int precisio
     TAKE(d.lam, double, 3 * nm);
     TAKE(d.lam_prev, double, 3 * nm);
     TAKE(d.lam_prev2, double, 3 * nm);
+    TAKE(d.lam_prev3, double, 3 * nm);
     TAKE(d.logz, double, nm);
     TAKE(d.logz_in, double, nm);
     TAKE(d.mat_id, int32_t, nm);
@@ -788,7 +789,7 @@ static int snap_fields(otm_handle *h, SnapField *f)
     f[k++] = {D.nflags, 1, 0}; f[k++] = {D.ngid, 8, 0};
     f[k++] = {D.xp, 32, 1}; f[k++] = {D.xp_prev, 32, 1}; f[k++] = {D.F, 72, 1}; f[k++] = {D.dF, 72, 1}; f[k++] = {D.be, 48, 1};
     f[k++] = {D.sig, 48, 1}; f[k++] = {D.vol, 8, 1}; f[k++] = {D.mass, 8, 1}; f[k++] = {D.ebar, 8, 1};
-    f[k++] = {D.T, 8, 1}; f[k++] = {D.rate, 8, 1}; f[k++] = {D.lam, 24, 1}; f[k++] = {D.lam_prev, 24, 1}; f[k++] = {D.lam_prev2, 24, 1};
+    f[k++] = {D.T, 8, 1}; f[k++] = {D.rate, 8, 1}; f[k++] = {D.lam, 24, 1}; f[k++] = {D.lam_prev, 24, 1}; f[k++] = {D.lam_prev2, 24, 1}; f[k++] = {D.lam_prev3, 24, 1};
     f[k++] = {D.logz, 8, 1};
     f[k++] = {D.logz_in, 8, 1}; f[k++] = {D.mat_id, 4, 1}; f[k++] = {D.mgid, 8, 1}; f[k++] = {D.cnt, 4, 1};
     f[k++] = {D.newton_it, 4, 1}; f[k++] = {D.failed, 1, 1};

@@ -33,8 +33,8 @@ struct GridDev {
 
 // where the LME solve of k_lme starts, and what it records:
 //   kLmePlain: at the stored lambda; lam_prev := the solution (initial supports, refresh)
-//   kLmeStep : at 3 lambda_n - 3 lambda_{n-1} + lambda_{n-2} (quadratic extrapolation in time);
-//              lam_prev2 := lambda_{n-1}, lam_prev := lambda_n
+//   kLmeStep : at 4 lambda_n - 6 lambda_{n-1} + 4 lambda_{n-2} - lambda_{n-3} (cubic extrapolation
+//              in time); lam_prev3, lam_prev2, lam_prev := lambda_{n-2}, lambda_{n-1}, lambda_n
 //   kLmeKeep : at the stored lambda; lam_prev kept (snapshot restore, the repeated solve after
 //              node insertion)
 constexpr int kLmePlain = 0, kLmeStep = 1, kLmeKeep = 2;
@@ -79,7 +79,7 @@ struct Dev {
     // material points
     double4_32a *xp, *xp_prev;       // position and the position of the previous step
     double *F, *dF, *be, *sig, *vol, *mass, *ebar, *T, *rate, *lam, *logz, *logz_in;
-    double *lam_prev, *lam_prev2;    // lambda of the two steps before (start extrapolation)
+    double *lam_prev, *lam_prev2, *lam_prev3;   // lambda of the three steps before (start extrapolation)
     int32_t *mat_id, *cnt, *newton_it;
     uint8_t *failed;                 // fracture flags of the step
     uint8_t *lme_fail;               // LME failures of the step (node insertion)

@@ -461,6 +461,7 @@ __global__ void k_init_state(const Dev D, double T0)
         D.lam[3 * p] = D.lam[3 * p + 1] = D.lam[3 * p + 2] = 0.0;
         D.lam_prev[3 * p] = D.lam_prev[3 * p + 1] = D.lam_prev[3 * p + 2] = 0.0;
         D.lam_prev2[3 * p] = D.lam_prev2[3 * p + 1] = D.lam_prev2[3 * p + 2] = 0.0;
+        D.lam_prev3[3 * p] = D.lam_prev3[3 * p + 1] = D.lam_prev3[3 * p + 2] = 0.0;
         D.logz[p] = 0.0;
         D.logz_in[p] = 0.0;
         D.failed[p] = 0;

@@ -677,13 +677,14 @@ __device__ __forceinline__ void lme_record(const Dev &D, int64_t p, double l0, d
 {
     if (D.lme_mode == kLmeStep) {
         for (int i = 0; i < 3; i++) {
+            D.lam_prev3[3 * p + i] = D.lam_prev2[3 * p + i];
             D.lam_prev2[3 * p + i] = D.lam_prev[3 * p + i];
             D.lam_prev[3 * p + i] = D.lam[3 * p + i];
         }
     } else if (D.lme_mode == kLmePlain) {
-        D.lam_prev[3 * p] = D.lam_prev2[3 * p] = l0;
-        D.lam_prev[3 * p + 1] = D.lam_prev2[3 * p + 1] = l1;
-        D.lam_prev[3 * p + 2] = D.lam_prev2[3 * p + 2] = l2;
+        D.lam_prev[3 * p] = D.lam_prev2[3 * p] = D.lam_prev3[3 * p] = l0;
+        D.lam_prev[3 * p + 1] = D.lam_prev2[3 * p + 1] = D.lam_prev3[3 * p + 1] = l1;
+        D.lam_prev[3 * p + 2] = D.lam_prev2[3 * p + 2] = D.lam_prev3[3 * p + 2] = l2;
     }
     D.lam[3 * p] = l0;
     D.lam[3 * p + 1] = l1;
@@ -723,14 +724,16 @@ __global__ void __launch_bounds__(kLmeWarps * kWarp) k_lme(const Dev D)
             W.q[k] = fma(-beta_s, fma(z, z, fma(y, y, x * x)), -shift_s);
         }
         if (lane == 0) {
-            // Eq. 14: the warm start is the previous step's lambda, or (within a step) the
-            // quadratic through the last three solutions, 3 l_n - 3 l_{n-1} + l_{n-2}: while
-            // the material deforms smoothly one Newton step from it meets the tolerance
+            // Eq. 14: the warm start is the previous step's lambda, or (within a step) the cubic
+            // through the last four solutions: while the material deforms smoothly one Newton
+            // step from it meets the tolerance
             double l0 = D.lam[3 * p], l1 = D.lam[3 * p + 1], l2 = D.lam[3 * p + 2];
             if (D.lme_mode == kLmeStep) {
-                l0 = fma(3.0, l0 - D.lam_prev[3 * p], D.lam_prev2[3 * p]);
-                l1 = fma(3.0, l1 - D.lam_prev[3 * p + 1], D.lam_prev2[3 * p + 1]);
-                l2 = fma(3.0, l2 - D.lam_prev[3 * p + 2], D.lam_prev2[3 * p + 2]);
+                // cubic: 4 l_n - 6 l_{n-1} + 4 l_{n-2} - l_{n-3}
+                const double *a1 = D.lam_prev + 3 * p, *a2 = D.lam_prev2 + 3 * p, *a3 = D.lam_prev3 + 3 * p;
+                l0 = fma(4.0, l0 + a2[0], -fma(6.0, a1[0], a3[0]));
+                l1 = fma(4.0, l1 + a2[1], -fma(6.0, a1[1], a3[1]));
+                l2 = fma(4.0, l2 + a2[2], -fma(6.0, a1[2], a3[2]));
             }
             M.trial[0] = M.ws[0] = l0;
             M.trial[1] = M.ws[1] = l1;
