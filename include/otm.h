@@ -231,8 +231,10 @@ int otm_adjoint_begin(otm_handle *h, void *adj_ws, size_t bytes, const double *x
  * masses and forces of step n: with next_snapshot NULL it recomputes step n (deterministic);
  * with next_snapshot a snapshot of state n+1 (device or page-locked host memory, as written by
  * otm_snapshot_save on this trajectory) it runs only the node update of step n and loads state
- * n+1, which is cheaper (no search, return map or Newton solve). Then it propagates the adjoint
- * to state n. The handle then holds state n+1. */
+ * n+1, which is cheaper (no search, return map or Newton solve); when the previous call of the
+ * same backward pass was the backward step of step n+1, the shape functions of state n+1 kept
+ * from it are copied instead of solved again. Then it propagates the adjoint to state n. The
+ * handle then holds state n+1 (its node-major contributions are regenerated by the next step). */
 int otm_adjoint_step(otm_handle *h, void *adj_ws, const void *next_snapshot);
 /* theta_bar[5] = d objective / d (A, B, n, C, m); dubar_host (n_nodes x 3, optional) =
  * d objective / d (displacement increments of the state the backward pass has reached). */

@@ -119,6 +119,7 @@ struct AdjDev {
     double4_32a *du_n;
     double *F_n, *be_n, *ebar_n, *T_n, *vol_n, *sig_n;
     double4_32a *shape_n;
+    double4_32a *shape_next;           // shape functions of state n+1 kept from the previous backward step
     int32_t *ids_n, *cnt_n, *noff_n;
     uint16_t *rank_n;
     // per-pair node contributions in node-major order
