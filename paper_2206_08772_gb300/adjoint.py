@@ -66,8 +66,11 @@ class RodObjectives(torch.autograd.Function):
         return torch.from_numpy(grad), None, None, None
 
 
-def backward_pass(sim: OTM, prob, steps: int, every: int, checkpoints: dict, final, xbar: np.ndarray) -> np.ndarray:
-    """d objective / d theta for the seed xbar = d objective / d final node positions."""
+def backward_pass(sim: OTM, prob, steps: int, every: int, checkpoints: dict, final, xbar: np.ndarray,
+                  recompute: bool = False) -> np.ndarray:
+    """d objective / d theta for the seed xbar = d objective / d final node positions. Each
+    backward step gets state n+1 from the recomputed segment's snapshots, or (recompute=True)
+    recomputes step n itself."""
     sim.restore(final)
     sim.adjoint_begin(xbar)
     seg_starts = sorted(checkpoints)
@@ -83,7 +86,10 @@ def backward_pass(sim: OTM, prob, steps: int, every: int, checkpoints: dict, fin
         end = checkpoints[s1] if s1 in checkpoints else final    # state s1
         for k in range(s1 - 1, s0 - 1, -1):
             sim.restore(states[k - s0])
-            sim.adjoint_step(states[k + 1 - s0] if k + 1 - s0 < len(states) else end)
+            if recompute:
+                sim.adjoint_step()
+            else:
+                sim.adjoint_step(states[k + 1 - s0] if k + 1 - s0 < len(states) else end)
         del states
     thb, dub = sim.adjoint_result()
     out = np.zeros(6)

@@ -90,3 +90,29 @@ def test_gpu_adjoint_against_finite_differences_with_replayed_supports():
             fd = (f[0][o] - f[1][o]) / (2 * hk)
             noise = 20 * np.finfo(float).eps * abs(vals[o].item()) / hk
             assert abs(fd - grads[o][k]) <= 1e-6 * abs(grads[o][k]) + noise, (k, o, fd, grads[o][k])
+
+
+def test_backward_from_snapshots_equals_backward_by_recompute():
+    """The backward steps that load state n+1 from the segment's snapshots (with the shape
+    functions of state n+1 kept from the previous backward step) give the same gradient as
+    backward steps that recompute step n."""
+    import math
+    from paper_2206_08772_gb300.adjoint import backward_pass, objectives_and_seeds
+    from paper_2206_08772_gb300.otm import OTM
+    steps, every = 9, 3
+    p = make_rod(THETA0)
+    out = []
+    for recompute in (False, True):
+        sim = OTM(p)
+        checkpoints = {0: sim.snapshot()}
+        for k in range(steps):
+            assert sim.step(1) == 0
+            if (k + 1) % every == 0 and k + 1 < steps:
+                checkpoints[k + 1] = sim.snapshot()
+        final = sim.snapshot()
+        _, seeds, _ = objectives_and_seeds(sim.get("node_x"), sim.get("node_mass"), p.h)
+        out.append(backward_pass(sim, p, steps, every, checkpoints, final, seeds[0] + seeds[1],
+                                 recompute=recompute))
+    scale = np.abs(out[1] * THETA0)
+    assert np.all(np.abs(out[0] - out[1]) * THETA0 <= 1e-13 * scale.max() + 1e-12 * scale), out
+    assert math.isfinite(out[0][5]) and out[0][5] != 0.0
