@@ -221,6 +221,7 @@ __global__ void __launch_bounds__(128) k_adj_rm(const Dev D, const AdjDev A)
     in.T = A.T_n[p];
     in.J = Jn;
     in.guess = D.rate[p] * D.dt;   // the recomputed step's own increment
+    in.Q0 = nullptr;
     RmOut out;
     return_map_point(M, D.dt, in, out);
     RmDetail o;

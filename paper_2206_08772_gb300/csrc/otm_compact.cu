@@ -116,7 +116,7 @@ cudaError_t erode_mps(Dev &D, int32_t *scan_tmp, int64_t *n_drop_host, cudaStrea
         void *p;
         size_t row;
     } fields[] = {{D.xp, 32}, {D.xp_prev, 32}, {D.F, 72}, {D.dF, 72}, {D.be, 48}, {D.sig, 48}, {D.vol, 8}, {D.mass, 8},
-                  {D.ebar, 8}, {D.T, 8}, {D.rate, 8}, {D.lam, 24}, {D.lam_prev, 24}, {D.lam_prev2, 24}, {D.lam_prev3, 24}, {D.logz, 8}, {D.logz_in, 8}, {D.mat_id, 4},
+                  {D.ebar, 8}, {D.T, 8}, {D.rate, 8}, {D.lam, 24}, {D.lam_prev, 24}, {D.lam_prev2, 24}, {D.lam_prev3, 24}, {D.Qe, 72}, {D.logz, 8}, {D.logz_in, 8}, {D.mat_id, 4},
                   {D.newton_it, 4}, {D.mgid, 8}};
     for (auto &f : fields)
         if ((e = compact_array(f.p, nm, f.row, keep, newidx, nn_new, tmp, s, launches)) != cudaSuccess) return e;

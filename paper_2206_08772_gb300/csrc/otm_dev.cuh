@@ -80,6 +80,7 @@ struct Dev {
     double4_32a *xp, *xp_prev;       // position and the position of the previous step
     double *F, *dF, *be, *sig, *vol, *mass, *ebar, *T, *rate, *lam, *logz, *logz_in;
     double *lam_prev, *lam_prev2, *lam_prev3;   // lambda of the three steps before (start extrapolation)
+    double *Qe;                      // eigenvectors of b^e from the last return map (9, row-major)
     int32_t *mat_id, *cnt, *newton_it;
     uint8_t *failed;                 // fracture flags of the step
     uint8_t *lme_fail;               // LME failures of the step (node insertion)

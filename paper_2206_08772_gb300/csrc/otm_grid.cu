@@ -462,6 +462,7 @@ __global__ void k_init_state(const Dev D, double T0)
         D.lam_prev[3 * p] = D.lam_prev[3 * p + 1] = D.lam_prev[3 * p + 2] = 0.0;
         D.lam_prev2[3 * p] = D.lam_prev2[3 * p + 1] = D.lam_prev2[3 * p + 2] = 0.0;
         D.lam_prev3[3 * p] = D.lam_prev3[3 * p + 1] = D.lam_prev3[3 * p + 2] = 0.0;
+        for (int i = 0; i < 9; i++) D.Qe[9 * p + i] = (i % 4 == 0) ? 1.0 : 0.0;
         D.logz[p] = 0.0;
         D.logz_in[p] = 0.0;
         D.failed[p] = 0;

@@ -967,6 +967,9 @@ __global__ void __launch_bounds__(128) k_return_map(const Dev D)
     in.ebar = D.ebar[p];
     in.T = D.T[p];
     in.guess = D.rate[p] * D.dt;   // the previous step's plastic increment
+    double Q0[9];
+    for (int i = 0; i < 9; i++) Q0[i] = D.Qe[9 * p + i];
+    in.Q0 = Q0;
     RmOut o;
     const int st = return_map_point(D.mat[D.mat_id[p]], D.dt, in, o);
     if (st != OTM_OK) {
@@ -980,6 +983,7 @@ __global__ void __launch_bounds__(128) k_return_map(const Dev D)
     D.ebar[p] = o.ebar;
     D.T[p] = o.T;
     D.rate[p] = o.rate;
+    for (int i = 0; i < 9; i++) D.Qe[9 * p + i] = o.Q[i];
     D.failed[p] = (uint8_t)(o.failed && D.allow_erode);
 }
 
@@ -1146,6 +1150,7 @@ __global__ void __launch_bounds__(128)
     in.ebar = ebar[p];
     in.T = T[p];
     in.guess = 0.0;
+    in.Q0 = nullptr;
     const double *Fn = F_new + 9 * p;
     in.J = Fn[0] * (Fn[4] * Fn[8] - Fn[5] * Fn[7]) - Fn[1] * (Fn[3] * Fn[8] - Fn[5] * Fn[6]) +
            Fn[2] * (Fn[3] * Fn[7] - Fn[4] * Fn[6]);

@@ -72,9 +72,12 @@ __device__ __forceinline__ void jc_sigma_y(const otm_material &M, double ebar_n,
 struct RmIn {
     double dF[9], be[6], ebar, T, J;
     double guess;      // start of the consistency iteration (e.g. the last step's increment); <= 0: none
+    const double *Q0;  // start basis of the eigen solver (row-major, columns the last step's
+                       // eigenvectors of b^e) or nullptr
 };
 struct RmOut {
     double sig[6], be[6], ebar, T, rate;
+    double Q[9];       // eigenvectors of the trial b^e (row-major, columns)
     bool failed;
 };
 
@@ -97,7 +100,27 @@ __device__ inline int return_map_point(const otm_material &M, double dt, const R
     for (int i = 0; i < 3; i++)
         for (int j = i + 1; j < 3; j++) A[i][j] = A[j][i] = 0.5 * (A[i][j] + A[j][i]);
     double Q[3][3];
-    jacobi_sym3(A, Q);
+    if (in.Q0) {
+        // in the last step's eigenbasis the trial b^e is nearly diagonal, so the Jacobi sweeps
+        // start close to convergence: A <- Q0^T A Q0, then Q = Q0 V
+        double T3[3][3], B[3][3], V[3][3];
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++)
+                T3[i][j] = A[i][0] * in.Q0[j] + A[i][1] * in.Q0[3 + j] + A[i][2] * in.Q0[6 + j];
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++)
+                B[i][j] = in.Q0[i] * T3[0][j] + in.Q0[3 + i] * T3[1][j] + in.Q0[6 + i] * T3[2][j];
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) A[i][j] = (i == j) ? B[i][i] : 0.5 * (B[i][j] + B[j][i]);
+        jacobi_sym3(A, V);
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++)
+                Q[i][j] = in.Q0[3 * i] * V[0][j] + in.Q0[3 * i + 1] * V[1][j] + in.Q0[3 * i + 2] * V[2][j];
+    } else {
+        jacobi_sym3(A, Q);
+    }
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) out.Q[3 * i + j] = Q[i][j];
     double e[3];
     for (int a = 0; a < 3; a++) {
         if (!(A[a][a] > 0.0)) return OTM_ERR_JACOBIAN;
