@@ -27,6 +27,10 @@
  *     eta = sign(p) * infinity where sigma_v <= 1e-12 |p| (no deviatoric stress left)
  *   - wall contact projects the node onto the plane, keeping the tangential increment
  *   - tool contact: normal projection plus Coulomb stick/slip at the penalty limit m/dt^2
+ *   - LME Newton: damped, stops at |r| <= newton_tol * h (1e-14 h in the scenarios); after a
+ *     failed warm start one more solve from lambda = 0
+ *   - node insertion (max_insert > 0): a node one spacing beyond an MP whose solve fails, away
+ *     from its support's centroid (see insert_nodes)
  */
 #include <math.h>
 #include <stdint.h>
