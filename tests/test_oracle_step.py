@@ -197,3 +197,22 @@ def test_node_insertion_capacity(orc):
     st = sim.step(34)
     c = sim.counts()
     assert st == -8 and c["err"] == -8 and c["n_nodes"] == p.n_nodes
+
+
+def test_lme_cold_start_after_a_failed_warm_start(orc):
+    """Reading of the Newton start: a warm start far from the solution puts nearly all weight on
+    one or two nodes (singular Hessian), so the damped Newton from it fails; the step's solve
+    then starts again from lambda = 0 and reaches the same shape functions as a fresh solve."""
+    p = small_rod(wall=False)
+    sim = orc.Sim(p)
+    N0, off0 = sim.get("N").copy(), sim.get("offsets").copy()
+    lam_far = np.tile(np.array([3.0e5, -2.0e5, 4.0e5]), (p.n_mps, 1))   # |lambda| h ~ 400
+    q = 5
+    ids = sim.get("ids")[off0[q]:off0[q + 1]]
+    d = sim.get("mp_x")[q] - sim.get("node_x")[ids]
+    st, *_ = orc.lme(d, p.beta, p.newton_tol * p.h, lam0=lam_far[q])
+    assert st == -4                       # the warm start alone fails
+    sim.set("lam", lam_far)
+    assert sim.refresh() == 0             # the retry from lambda = 0 succeeds
+    assert np.array_equal(sim.get("offsets"), off0)
+    assert np.abs(sim.get("N") - N0).max() <= 1e-12
