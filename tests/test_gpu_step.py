@@ -354,3 +354,16 @@ def test_frozen_topology_keeps_the_supports(OTM):
     e = OTM(scenarios.chip_block(h=0.02e-3, size=(0.4e-3, 0.2e-3, 0.1e-3), depth=0.06e-3, steps=2))
     with pytest.raises(Exception):
         e.freeze_topology(True)                                      # eroding problem: refused
+
+
+def test_lme_cold_start_after_a_failed_warm_start(orc, OTM):
+    """A far warm start makes the first Newton solve fail; the kernel solves again from
+    lambda = 0 and reaches the shape functions of a fresh solve (as the oracle does)."""
+    p = scenarios.taylor_rod(h=0.8e-3, R=3.2e-3, L=4.0e-3, wall=False)
+    g = OTM(p)
+    shape0 = g.get("shape")
+    g.set("lam", np.tile(np.array([3.0e5, -2.0e5, 4.0e5]), (p.n_mps, 1)))
+    assert g.refresh() == 0, g.error()
+    assert rel(g.get("shape"), shape0) <= 1e-12
+    o = orc.Sim(p)
+    assert rel(g.get("lam"), o.get("lam")) <= 1e-10
