@@ -216,3 +216,52 @@ def test_lme_cold_start_after_a_failed_warm_start(orc):
     assert sim.refresh() == 0             # the retry from lambda = 0 succeeds
     assert np.array_equal(sim.get("offsets"), off0)
     assert np.abs(sim.get("N") - N0).max() <= 1e-12
+
+
+def test_stabilisation_vanishes_on_affine_motion(orc):
+    """Eq. 7-8: the under-integration error e = x_I - x_p - dF (x_I,n-1 - x_p,n-1) is zero when a
+    step moves nodes and MPs affinely, so the stabilised residual equals the plain one there; a
+    non-affine increment makes it differ."""
+    G = np.array([[2e-3, 1e-3, -5e-4], [-7e-4, -1e-3, 3e-4], [4e-4, 6e-4, 1.5e-3]])
+    forces = {}
+    for eps in (0.0, 1e-3):
+        for affine in (True, False):
+            p = small_rod(wall=False)
+            p.eps_stab = eps * p.materials[0].E * p.h ** 2
+            p.node_du0 = p.node_x @ G.T
+            if not affine:
+                rng = np.random.default_rng(3)
+                p.node_du0 = p.node_du0 + rng.uniform(-1e-4, 1e-4, p.node_du0.shape) * p.h
+            sim = orc.Sim(p)
+            assert sim.step(2) == 0
+            forces[(eps, affine)] = sim.get("node_force")
+    scale = np.abs(forces[(0.0, True)]).max()
+    assert np.abs(forces[(1e-3, True)] - forces[(0.0, True)]).max() <= 1e-12 * scale
+    assert np.abs(forces[(1e-3, False)] - forces[(0.0, False)]).max() >= 1e-6 * scale
+
+
+def test_tool_contact_leaves_no_node_inside_the_tool(orc):
+    """Sec. 4.2 tool: after every step no free node lies inside the wedge of the rake face
+    (normal -e_x for rake 0) and the clearance face (7 deg), which moves with the tool."""
+    import math
+    h = 0.02e-3
+    p = scenarios.chip_block(h=h, size=(0.4e-3, 0.2e-3, 0.1e-3), depth=0.06e-3, embed=1.5 * h, steps=4)
+    c = p.contact
+    rake, clear = math.radians(c.tool_rake_deg), math.radians(c.tool_clearance_deg)
+    nr = np.array([-math.cos(rake), math.sin(rake)])
+    nf = np.array([math.sin(clear), -math.cos(clear)])
+    sim = orc.Sim(p)
+    inside0 = None
+    for k in range(4):
+        if k == 0:
+            x = sim.get("node_x")
+            rel_ = x[:, :2] - np.array([c.tool_x0, c.tool_tip_y])
+            inside0 = np.count_nonzero((rel_ @ nr < 0) & (rel_ @ nf < 0))
+        assert sim.step(1) == 0
+        x = sim.get("node_x")
+        free = (p.node_flags[sim.get("node_gid")] & 1) == 0
+        xt = c.tool_x0 - c.tool_velocity * (k + 1) * p.dt
+        rel_ = x[free, :2] - np.array([xt, c.tool_tip_y])
+        depth = np.minimum(-(rel_ @ nr), -(rel_ @ nf))       # > 0 inside the wedge
+        assert depth.max() <= 1e-12 * p.h
+    assert inside0 > 0                                         # the embedding did start inside
