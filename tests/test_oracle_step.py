@@ -265,3 +265,28 @@ def test_tool_contact_leaves_no_node_inside_the_tool(orc):
         depth = np.minimum(-(rel_ @ nr), -(rel_ @ nf))       # > 0 inside the wedge
         assert depth.max() <= 1e-12 * p.h
     assert inside0 > 0                                         # the embedding did start inside
+
+
+def test_erosion_removes_exactly_the_failed_points_and_their_orphan_nodes(orc):
+    """Sec. 4.2 fracture and the erosion reading: at rest the Johnson-Cook fracture strain is
+    (d1 + d2)(1 + 0)(1 + 0) = 0.16, so raising the plastic strain of a chosen set of MPs to 1
+    erodes exactly that set in the next step; nodes left with no MP within r_s (brute force)
+    are removed; both lists keep ascending IDs."""
+    h = 0.02e-3
+    p = scenarios.chip_block(h=h, size=(0.4e-3, 0.2e-3, 0.1e-3), depth=0.06e-3, steps=2)
+    p.contact.tool = False                      # nothing moves: only the chosen set fails
+    rng = np.random.default_rng(7)
+    corner = np.array([0.0, p.meta["size"][1], 0.0])
+    near = np.nonzero(np.linalg.norm(p.mp_x - corner, axis=1) <= 6 * h)[0]
+    E = np.union1d(rng.choice(p.n_mps, 40, replace=False), near)
+    sim = orc.Sim(p)
+    eb = np.zeros(p.n_mps)
+    eb[E] = 1.0
+    sim.set("ebar", eb)
+    assert sim.step(1) == 0
+    assert np.array_equal(sim.get("mp_gid"), np.setdiff1d(np.arange(p.n_mps), E))
+    xp = sim.get("mp_x")
+    orphan = [i for i in range(p.n_nodes)
+              if not np.any(((xp - p.node_x[i]) ** 2).sum(1) <= p.rs2)]
+    assert len(orphan) > 0
+    assert np.array_equal(sim.get("node_gid"), np.setdiff1d(np.arange(p.n_nodes), orphan))
