@@ -26,6 +26,13 @@
  *  - Fields come back in ascending ID order (erosion removes entries, never reorders them).
  *  - After an error the state is that of the failing step, partially updated (the oracle
  *    behaves the same way); otm_error_detail names the code and the smallest offending ID.
+ *    otm_keep_last_good makes otm_step leave the state at the last good step instead.
+ *  - Device reset: the library keeps two pieces of module data per device (the table of its
+ *    FP64 exponential and the allocation-free search's scratch address), set up by the first
+ *    call on that device. A reset of the device or of its primary context (cudaDeviceReset)
+ *    discards module data: otm_init checks for that and sets the table up again, so a reset must
+ *    be followed by otm_init before the stand-alone kernels are used; the allocation-free search
+ *    is not supported after a reset in the same process.
  */
 #ifndef OTM_H
 #define OTM_H
@@ -145,6 +152,17 @@ int otm_step(otm_handle *h, int32_t n_steps);
  * (the host reads how many entries leave or arrive before it sizes the following launches). */
 int otm_step_async(otm_handle *h, int32_t n_steps);
 
+/* Keep the last good step. With buf set (caller-owned, 256-byte aligned, device or page-locked
+ * host memory of at least otm_snapshot_bytes), otm_step and otm_step_async save the state into
+ * buf before every step and synchronise after it; a step that raises an error is undone by
+ * loading buf (the state after the last good step, shape functions regenerated bit for bit, as
+ * otm_snapshot_load), the error stays recorded for otm_error_detail, and the call returns it.
+ * Later steps then return the same error until otm_snapshot_load or otm_refresh clears it (the
+ * caller's resume path: change the state, refresh, step on). Costs one snapshot copy and one
+ * synchronisation per step. buf = NULL turns it off. OTM_ERR_ARG for a misaligned or short buf.
+ * (Without it, the state after an error is that of the failing step, partially updated.) */
+int otm_keep_last_good(otm_handle *h, void *buf, size_t bytes);
+
 /* Current sizes (host-side view; exact after otm_step returns). */
 int otm_counts(otm_handle *h, int64_t *n_nodes, int64_t *n_mps, int64_t *n_pairs, int64_t *step);
 
@@ -176,6 +194,34 @@ int otm_freeze_topology(otm_handle *h, int32_t on);
  * index (nothing runs), OTM_ERR_CAPACITY if a node gets more than 65,535 influences; not for
  * problems that erode MPs or insert nodes. Synchronises. */
 int otm_step_with_supports(otm_handle *h, const int32_t *counts, const int32_t *ids);
+
+/* The current supports (Algorithm 3 output of the last step) as a compact CSR in caller-owned
+ * DEVICE memory: offsets (n_mps + 1 int32; offsets[0] = 0, offsets[p+1] - offsets[p] = support
+ * size of MP p) and ids (at least *n_pairs int32; MP p's row at ids[offsets[p]...], in the
+ * library's own row order, i.e. linked-cell order, so that otm_step_with_supports_csr replays it
+ * bit for bit). ids_cap: capacity of ids in entries; if the state has more pairs,
+ * OTM_ERR_CAPACITY (offsets and *n_pairs are written, ids is not). Enqueued on the handle's
+ * stream; synchronises once to read the pair count. */
+int otm_supports_export(otm_handle *h, int32_t *offsets, int32_t *ids, int64_t ids_cap, int64_t *n_pairs);
+
+/* otm_step_with_supports with the new supports given as a CSR in DEVICE memory (offsets:
+ * n_mps + 1 int32, ids: ids_len int32, as written by otm_supports_export; any order within a
+ * row). Before anything reads through them, a kernel checks every row: 0 <= offsets[p] and
+ * offsets[p+1] <= ids_len, 1 <= offsets[p+1] - offsets[p] <= max_support, every ID in
+ * [0, n_nodes); a violation gives OTM_ERR_ARG and nothing runs. The caller must provide n_mps + 1
+ * readable offsets. Not for problems that erode MPs or insert nodes. Synchronises. */
+int otm_step_with_supports_csr(otm_handle *h, const int32_t *offsets, const int32_t *ids, int64_t ids_len);
+
+/* The linked-cell grid of Algorithm 3 (step 1) for the current node positions, rebuilt by this
+ * call and copied to host memory: origin[3] = componentwise minimum of the node positions,
+ * dims[3] = floor((max - min) / cell_size) + 1, *n_cells = their product; cell_start (optional,
+ * n_cells + 1 int32, capacity cap_cells entries, else OTM_ERR_CAPACITY): the nodes of cell
+ * c = (iz * dims[1] + iy) * dims[0] + ix are sorted[cell_start[c] .. cell_start[c+1]); sorted
+ * (optional, n_nodes int32): node indices (ID order) ordered by (cell, index). A grid that
+ * cannot be built returns its error (OTM_ERR_NONFINITE, OTM_ERR_CAPACITY), which then stays
+ * recorded like a step's. Synchronises. */
+int otm_grid_cells(otm_handle *h, double *origin, int32_t *dims, int64_t *n_cells, int32_t *cell_start,
+                   int64_t cap_cells, int32_t *sorted);
 
 /* First error recorded on the device: its code and the smallest offending ID. Synchronises. */
 int otm_error_detail(otm_handle *h, int32_t *code, int64_t *first_id);
@@ -236,9 +282,15 @@ int otm_adjoint_begin(otm_handle *h, void *adj_ws, size_t bytes, const double *x
  * from it are copied instead of solved again. Then it propagates the adjoint to state n. The
  * handle then holds state n+1 (its node-major contributions are regenerated by the next step). */
 int otm_adjoint_step(otm_handle *h, void *adj_ws, const void *next_snapshot);
-/* theta_bar[5] = d objective / d (A, B, n, C, m); dubar_host (n_nodes x 3, optional) =
- * d objective / d (displacement increments of the state the backward pass has reached). */
-int otm_adjoint_result(otm_handle *h, void *adj_ws, double *theta_bar, double *dubar_host);
+/* theta_bar[6] = d objective / d (A, B, n, C, m, s): the Johnson-Cook constants of material 0
+ * and a scalar s on which the initial displacement increments depend, through du0_ds (host,
+ * n_nodes x 3, optional: d(du_I at step 0)/ds; NULL gives theta_bar[5] = 0). For an impact
+ * with du_0 = -v0 dt e_z on every node, du0_ds = (0, 0, -dt) per node makes theta_bar[5] the
+ * derivative with respect to the impact velocity v0. The chain rule is applied once the backward
+ * pass has reached step 0. dubar_host (n_nodes x 3, optional) = d objective / d (displacement
+ * increments of the state the backward pass has reached). */
+int otm_adjoint_result(otm_handle *h, void *adj_ws, const double *du0_ds, double *theta_bar,
+                       double *dubar_host);
 
 /* ---------------------------------------------------------------------------------------
  * Stand-alone kernels (device pointers, caller-owned; enqueued on `stream`, not synchronised)

@@ -98,7 +98,11 @@ _SIGS = {
     "otm_adjoint_step": (C.c_int, [_P, _P, _P]),
     "otm_freeze_topology": (C.c_int, [_P, C.c_int32]),
     "otm_step_with_supports": (C.c_int, [_P, _P, _P]),
-    "otm_adjoint_result": (C.c_int, [_P, _P, _P, _P]),
+    "otm_adjoint_result": (C.c_int, [_P, _P, _P, _P, _P]),
+    "otm_supports_export": (C.c_int, [_P, _P, _P, _I64, _P]),
+    "otm_keep_last_good": (C.c_int, [_P, _P, _SZ]),
+    "otm_step_with_supports_csr": (C.c_int, [_P, _P, _P, _I64]),
+    "otm_grid_cells": (C.c_int, [_P, _P, _P, _P, _P, _I64, _P]),
 }
 
 

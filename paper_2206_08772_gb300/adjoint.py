@@ -91,11 +91,11 @@ def backward_pass(sim: OTM, prob, steps: int, every: int, checkpoints: dict, fin
             else:
                 sim.adjoint_step(states[k + 1 - s0] if k + 1 - s0 < len(states) else end)
         del states
-    thb, dub = sim.adjoint_result()
-    out = np.zeros(6)
-    out[:5] = thb
-    out[5] = -prob.dt * dub[:, 2].sum()   # du_0 = (0, 0, -v0 dt) on every node
-    return out
+    # du_0 = (0, 0, -v0 dt) on every node: d(du_0)/d(v0) = (0, 0, -dt)
+    du0_dv0 = np.zeros((prob.n_nodes, 3))
+    du0_dv0[:, 2] = -prob.dt
+    thb, _ = sim.adjoint_result(du0_dv0)
+    return thb
 
 
 def rod_objectives(theta: torch.Tensor, make_problem, steps: int, every: int | None = None) -> torch.Tensor:

@@ -35,9 +35,10 @@ struct GridDev {
 //   kLmePlain: at the stored lambda; lam_prev := the solution (initial supports, refresh)
 //   kLmeStep : at 4 lambda_n - 6 lambda_{n-1} + 4 lambda_{n-2} - lambda_{n-3} (cubic extrapolation
 //              in time); lam_prev3, lam_prev2, lam_prev := lambda_{n-2}, lambda_{n-1}, lambda_n
-//   kLmeKeep : at the stored lambda; lam_prev kept (snapshot restore, the repeated solve after
-//              node insertion)
-constexpr int kLmePlain = 0, kLmeStep = 1, kLmeKeep = 2;
+//   kLmeKeep : at the stored lambda; lam_prev kept (snapshot restore)
+//   kLmeRetry: the repeated solve after node insertion: as kLmeKeep, except that the MPs flagged
+//              in lme_fail (solved again from lambda_n) restart their history as in kLmePlain
+constexpr int kLmePlain = 0, kLmeStep = 1, kLmeKeep = 2, kLmeRetry = 3;
 
 // constants of the support search, derived once on the host from the cell size and r_s^2
 struct SearchConst {
@@ -85,6 +86,7 @@ struct Dev {
     uint8_t *failed;                 // fracture flags of the step
     uint8_t *lme_fail;               // LME failures of the step (node insertion)
     int32_t *n_fail;                 // their count
+    int32_t *flag;                   // one int of scratch for host-read checks (argument validation)
     int64_t *mgid;
     // pairs: MP-major padded rows (ids, shape, rank) and node-major contributions
     int32_t *ids;
@@ -332,7 +334,7 @@ cudaError_t launch_search(const Dev &D, cudaStream_t s, long long *launches);
 cudaError_t launch_kin_search(const Dev &D, cudaStream_t s, long long *launches);
 cudaError_t launch_lme(const Dev &D, cudaStream_t s, long long *launches);
 cudaError_t launch_node_offsets(const Dev &D, int32_t *tmp, cudaStream_t s, long long *launches);
-cudaError_t exp_table_setup();
+cudaError_t exp_table_setup(bool verify = false);
 cudaError_t launch_exp_selftest(const double *x, int64_t n, double *mine, double *ref, cudaStream_t s);
 cudaError_t launch_node_update(const Dev &D, double t_next, cudaStream_t s, long long *launches);
 cudaError_t launch_rows_to_dense(const void *src, size_t pitch, size_t width, int64_t rows, void *dst, cudaStream_t s);
@@ -352,6 +354,11 @@ cudaError_t build_search_grid(const double *node_x, int64_t nn, double cell, Sea
 size_t lme_smem_bytes(int S, int warps);
 cudaError_t launch_adjoint_backward(const Dev &D, const AdjDev &A, cudaStream_t s, long long *launches);
 cudaError_t launch_rebuild_ranks(const Dev &D, cudaStream_t s, long long *launches);
+cudaError_t launch_csr_gather(const Dev &D, const int32_t *off, int32_t *ids, cudaStream_t s, long long *launches);
+cudaError_t launch_csr_check(const int32_t *off, const int32_t *ids, int64_t nm, int S, int64_t len, int64_t nn,
+                             int32_t *bad, cudaStream_t s, long long *launches);
+cudaError_t launch_csr_scatter(const Dev &D, const int32_t *off, const int32_t *ids, cudaStream_t s,
+                               long long *launches);
 cudaError_t insert_nodes(Dev &D, int32_t *scan_tmp, int64_t n_fail, int64_t next_gid, cudaStream_t s,
                          long long *launches);
 cudaError_t raise_flagged(const Dev &D, int code, cudaStream_t s, long long *launches);

@@ -53,7 +53,9 @@ __global__ void k_bbox(const double4_32a *__restrict__ x, int64_t n, GridDev *g)
 __global__ void k_grid_setup(GridDev *g, double cell, int max_cells, unsigned long long *err)
 {
     if (threadIdx.x != 0) return;
-    long long total = 1;
+    // the cell count is formed in FP64: each axis is at most max_cells (< 2^31), so the product
+    // is below 2^93 and cannot wrap, and any product above max_cells is reported as capacity
+    double total = 1.0;
     bool ok = true;
     for (int d = 0; d < 3; d++) {
         double lo = dkey_inv(g->key_lo[d]), hi = dkey_inv(g->key_hi[d]);
@@ -65,14 +67,14 @@ __global__ void k_grid_setup(GridDev *g, double cell, int max_cells, unsigned lo
             continue;
         }
         double nd = floor(__ddiv_rn(__dsub_rn(hi, lo), cell)) + 1.0;
-        if (nd > (double)max_cells) {
+        if (!(nd <= (double)max_cells)) {
             ok = false;
             nd = 0;
         }
         g->dims[d] = (int)nd;
-        total *= (long long)nd;
+        total *= nd;
     }
-    if (ok && total > (long long)max_cells) ok = false;
+    if (ok && !(total <= (double)max_cells)) ok = false;
     if (!ok) raise_error(err, OTM_ERR_CAPACITY, 0);
     g->n_cells = ok ? (int)total : 0;
 }

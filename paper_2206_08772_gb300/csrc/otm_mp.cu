@@ -45,8 +45,12 @@ constexpr int kExpNmax = 1021 * 1024 + 1023;
 static __device__ double g_exp2_table[kExpTable];
 
 // Fill g_exp2_table on the current device (first call per device; a synchronous copy, so it
-// belongs before any stream capture: otm_init and the stand-alone entries call it).
-cudaError_t exp_table_setup()
+// belongs before any stream capture: otm_init and the stand-alone entries call it). With
+// `verify`, a device whose table was already filled is checked again (a synchronous 8-byte read
+// of 2^0 = 1): module data is lost when the device or its primary context is reset, and the
+// table is then filled anew. otm_init verifies; the stand-alone entries, which must stay free of
+// synchronisation once set up, do not.
+cudaError_t exp_table_setup(bool verify)
 {
     static std::mutex mu;
     static bool done[64];
@@ -55,6 +59,12 @@ cudaError_t exp_table_setup()
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(mu);
+    if (done[dev] && verify) {
+        double t0 = 0.0;
+        e = cudaMemcpyFromSymbol(&t0, g_exp2_table, sizeof(double));
+        if (e != cudaSuccess) return e;
+        if (t0 != 1.0) done[dev] = false;
+    }
     if (done[dev]) return cudaSuccess;
     double host[kExpTable];
     for (int j = 0; j < kExpTable; j++) host[j] = std::exp2((double)j / (double)kExpTable);
@@ -681,7 +691,9 @@ __device__ __forceinline__ void lme_record(const Dev &D, int64_t p, double l0, d
             D.lam_prev2[3 * p + i] = D.lam_prev[3 * p + i];
             D.lam_prev[3 * p + i] = D.lam[3 * p + i];
         }
-    } else if (D.lme_mode == kLmePlain) {
+    } else if (D.lme_mode == kLmePlain || (D.lme_mode == kLmeRetry && D.lme_fail[p])) {
+        // a plain start, or an MP solved again after node insertion: its previous solutions were
+        // not one step apart from this one, so the history restarts at the new solution
         D.lam_prev[3 * p] = D.lam_prev2[3 * p] = D.lam_prev3[3 * p] = l0;
         D.lam_prev[3 * p + 1] = D.lam_prev2[3 * p + 1] = D.lam_prev3[3 * p + 1] = l1;
         D.lam_prev[3 * p + 2] = D.lam_prev2[3 * p + 2] = D.lam_prev3[3 * p + 2] = l2;

@@ -4,10 +4,14 @@
 //
 // Determinism without float atomics and without sorting: every pair contribution is converted
 // to a fixed-point integer whose least significant bit is 2^(Emax - 110) (FP64 path, 128-bit
-// accumulators) or 2^(Emax - 48) (mixed path, 64-bit accumulators), Emax being the largest
+// accumulators) or 2^(Emax - 46) (mixed path, 64-bit accumulators), Emax being the largest
 // binary exponent of that field over all pairs of the step. Integer addition is associative,
 // so the sum is exact and independent of the order in which the influence list was filled.
-// Terms below the least significant bit (2^-110 of the largest term) are truncated.
+// Terms below the least significant bit (2^-110, resp. 2^-46, of the largest term) are truncated.
+//
+// Headroom: a term is below 2^(Emax + 1), i.e. below 2^111 (FP64) or 2^47 (mixed) units, and a
+// node has at most 65,536 influences (the search raises OTM_ERR_CAPACITY beyond), so a node sum
+// stays below 2^127 resp. 2^63 and fits the signed accumulator whatever the signs.
 #include "otm_dev.cuh"
 
 namespace otm {
@@ -74,7 +78,7 @@ __device__ __forceinline__ long long to_fixed64(float v, int emax)
     const int ef = (int)((b >> 23) & 0xff);
     if (ef == 0 || ef == 0xff) return 0;
     const long long m = (long long)((b & 0x007FFFFFu) | 0x00800000u);
-    const int sh = (ef - 127) - emax + 25;   // value = m * 2^(e - 23); lsb = 2^(emax - 48)
+    const int sh = (ef - 127) - emax + 23;   // value = m * 2^(e - 23); lsb = 2^(emax - 46)
     long long r;
     if (sh < -23) return 0;
     r = (sh < 0) ? (m >> (-sh)) : (m << sh);
@@ -149,10 +153,10 @@ __global__ void __launch_bounds__(kNodeWarps * kWarp) k_node_update(const Dev D,
             sz += to_fixed64(c.w, ef);
         }
         sm = warp_sum64(sm); sx = warp_sum64(sx); sy = warp_sum64(sy); sz = warp_sum64(sz);
-        m = ldexp((double)sm, em - 48);
-        rx = ldexp((double)sx, ef - 48);
-        ry = ldexp((double)sy, ef - 48);
-        rz = ldexp((double)sz, ef - 48);
+        m = ldexp((double)sm, em - 46);
+        rx = ldexp((double)sx, ef - 46);
+        ry = ldexp((double)sy, ef - 46);
+        rz = ldexp((double)sz, ef - 46);
     } else {
         I128 sm = {0, 0}, sx = {0, 0}, sy = {0, 0}, sz = {0, 0};
         for (int k = lane; k < L; k += kWarp) {

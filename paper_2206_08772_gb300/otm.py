@@ -157,6 +157,24 @@ class OTM:
         check(L.otm_snapshot_save(self._h, C.c_void_p(ptr)), "otm_snapshot_save")
         return (buf, ptr)
 
+    def keep_last_good(self, on: bool = True, host: bool = False):
+        """otm_keep_last_good: every step first saves the state into a buffer kept by this object,
+        and a failing step is undone (the state stays at the last good step)."""
+        L = _lib.load()
+        if not on:
+            check(L.otm_keep_last_good(self._h, None, 0), "otm_keep_last_good")
+            self._keep = None
+            return
+        nb = C.c_size_t(0)
+        check(L.otm_snapshot_bytes(self._h, C.byref(nb)), "otm_snapshot_bytes")
+        if host:
+            buf = torch.empty(nb.value + 256, dtype=torch.uint8, pin_memory=True)
+            ptr = (buf.data_ptr() + 255) & ~255
+        else:
+            buf, ptr = self._aligned(nb.value)
+        check(L.otm_keep_last_good(self._h, C.c_void_p(ptr), nb.value), "otm_keep_last_good")
+        self._keep = buf
+
     def restore(self, snap):
         check(_lib.load().otm_snapshot_load(self._h, C.c_void_p(snap[1])), "otm_snapshot_load")
 
@@ -180,15 +198,62 @@ class OTM:
             raise ValueError("ids must be (n_mps, max_support)")
         return _lib.load().otm_step_with_supports(self._h, _ptr(c), _ptr(i))
 
+    def supports_export(self, offsets: torch.Tensor | None = None, ids: torch.Tensor | None = None):
+        """The current supports as device tensors (offsets [n_mps + 1], ids [n_pairs], int32) in
+        the library's row order; given buffers are filled (ids must be large enough)."""
+        L = _lib.load()
+        nm = self.counts()["n_mps"]
+        if offsets is None:
+            offsets = torch.empty(nm + 1, dtype=torch.int32, device=self.device)
+        npairs = C.c_int64(0)
+        if ids is None:
+            probe = torch.empty(1, dtype=torch.int32, device=self.device)
+            st = L.otm_supports_export(self._h, C.c_void_p(offsets.data_ptr()), C.c_void_p(probe.data_ptr()), 0,
+                                       C.byref(npairs))
+            if st not in (0, _lib.ERR_CAPACITY):
+                check(st, "otm_supports_export")
+            ids = torch.empty(max(npairs.value, 1), dtype=torch.int32, device=self.device)
+        assert offsets.dtype == torch.int32 and ids.dtype == torch.int32 and offsets.numel() == nm + 1
+        check(L.otm_supports_export(self._h, C.c_void_p(offsets.data_ptr()), C.c_void_p(ids.data_ptr()),
+                                    ids.numel(), C.byref(npairs)), "otm_supports_export")
+        return offsets, ids[:npairs.value]
+
+    def step_with_supports_csr(self, offsets: torch.Tensor, ids: torch.Tensor) -> int:
+        """One step whose new supports are the given device CSR (see otm_step_with_supports_csr)."""
+        assert offsets.is_cuda and ids.is_cuda and offsets.dtype == torch.int32 and ids.dtype == torch.int32
+        assert offsets.is_contiguous() and ids.is_contiguous()
+        return _lib.load().otm_step_with_supports_csr(self._h, C.c_void_p(offsets.data_ptr()),
+                                                      C.c_void_p(ids.data_ptr()), ids.numel())
+
+    def grid_cells(self):
+        """The linked-cell grid of the current node positions: (origin[3], dims[3], cell_start
+        [n_cells + 1], sorted node indices [n_nodes])."""
+        L = _lib.load()
+        origin = np.zeros(3)
+        dims = np.zeros(3, np.int32)
+        nc = C.c_int64(0)
+        check(L.otm_grid_cells(self._h, _ptr(origin), _ptr(dims), C.byref(nc), None, 0, None), "otm_grid_cells")
+        cs = np.zeros(nc.value + 1, np.int32)
+        srt = np.zeros(self.counts()["n_nodes"], np.int32)
+        check(L.otm_grid_cells(self._h, _ptr(origin), _ptr(dims), C.byref(nc), _ptr(cs), cs.size, _ptr(srt)),
+              "otm_grid_cells")
+        return origin, dims, cs, srt
+
     def adjoint_step(self, next_snapshot=None):
         """One backward step from state n (held); next_snapshot (optional) holds state n+1."""
         nxt = C.c_void_p(next_snapshot[1]) if next_snapshot is not None else C.c_void_p(0)
         check(_lib.load().otm_adjoint_step(self._h, C.c_void_p(self._adj_ptr), nxt), "otm_adjoint_step")
 
-    def adjoint_result(self):
-        thb = np.zeros(5)
+    def adjoint_result(self, du0_ds: np.ndarray | None = None):
+        """(theta_bar[6], dL/d du): gradients w.r.t. (A, B, n, C, m) and, with du0_ds (the
+        derivative of the initial increments w.r.t. a scalar s), w.r.t. s (see otm_adjoint_result)."""
+        thb = np.zeros(6)
         dub = np.zeros((self.counts()["n_nodes"], 3))
-        check(_lib.load().otm_adjoint_result(self._h, C.c_void_p(self._adj_ptr), _ptr(thb), _ptr(dub)),
+        d = None if du0_ds is None else np.ascontiguousarray(du0_ds, dtype=np.float64)
+        if d is not None and d.shape != dub.shape:
+            raise ValueError("du0_ds must be (n_nodes, 3)")
+        check(_lib.load().otm_adjoint_result(self._h, C.c_void_p(self._adj_ptr),
+                                             _ptr(d) if d is not None else None, _ptr(thb), _ptr(dub)),
               "otm_adjoint_result")
         return thb, dub
 

@@ -102,22 +102,6 @@ def test_determinism(OTM, precision):
         assert np.array_equal(a, b)
 
 
-def test_error_status_nonconvergence(OTM):
-    """A point far outside its support's hull makes the Newton solve fail: the step reports
-    OTM_ERR_LME_NOCONV with the point's ID, and the GPU stays usable."""
-    p = scenarios.taylor_rod(h=0.8e-3, R=3.2e-3, L=4.0e-3, wall=False)
-    s = OTM(p)
-    xp = s.get("mp_x")
-    xp[7] += np.array([5.0e-3, 0.0, 0.0])     # pushed radially out of the rod (R = 3.2 mm)
-    s.set("mp_x", xp)
-    st = s.refresh()
-    code, fid = s.error()
-    assert st == code
-    assert code in (-4, -8)
-    s2 = OTM(p)
-    assert s2.step(2) == 0
-
-
 def chip_case(embed_h):
     h = 0.02e-3
     return scenarios.chip_block(h=h, size=(0.4e-3, 0.2e-3, 0.1e-3), depth=0.06e-3, embed=embed_h * h, steps=8)
