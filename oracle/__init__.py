@@ -120,6 +120,8 @@ def lib():
             L.orc_adj_destroy.argtypes = [_P]
             L.orc_adj_result.restype = None
             L.orc_adj_result.argtypes = [_P, _P, _P]
+            L.orc_tool_contact.restype = None
+            L.orc_tool_contact.argtypes = [_P, C.c_double, _P, _P]
             L.orc_adjoint_step.restype = C.c_int
             L.orc_adjoint_step.argtypes = [_P, _P, _P]
             assert L.orc_sizeof_params() == C.sizeof(Params)
@@ -261,6 +263,15 @@ def grid(node_x: np.ndarray, cell_size: float):
     return origin, dims, cs, srt
 
 
+def tool_contact(prob, t_next: float, du: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """The oracle's tool contact (Sec. 4.2) applied to one node: returns the new position."""
+    P = params_struct(prob)
+    du = np.ascontiguousarray(du, np.float64)
+    out = np.ascontiguousarray(x, np.float64).copy()
+    lib().orc_tool_contact(C.byref(P), t_next, _ptr(du), _ptr(out))
+    return out
+
+
 def kinematics(ids, N, dN, node_x, node_du):
     ids = np.ascontiguousarray(ids, np.int32)
     N = np.ascontiguousarray(N, np.float64)
@@ -282,7 +293,8 @@ FIELDS = dict(node_x=(0, 3, np.float64), node_du=(1, 3, np.float64), node_mass=(
               ebar=(9, 1, np.float64), T=(10, 1, np.float64), lam=(11, 3, np.float64),
               offsets=(12, 1, np.int64), ids=(13, 1, np.int32), N=(14, 1, np.float64),
               dN=(15, 3, np.float64), node_gid=(16, 1, np.int64), mp_gid=(17, 1, np.int64),
-              newton_it=(18, 1, np.int32), rate=(19, 1, np.float64))
+              newton_it=(18, 1, np.int32), rate=(19, 1, np.float64), mp_x_prev=(20, 3, np.float64),
+              node_x_prev=(21, 3, np.float64), dF=(22, 9, np.float64))
 
 
 class Sim:

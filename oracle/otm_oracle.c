@@ -1004,6 +1004,9 @@ int orc_sim_get(const orc_sim *s, int32_t field, void *dst, int64_t bytes)
     case 17: src = s->mp_gid; need = 8 * s->nm; break;
     case 18: src = s->newton_it; need = 4 * s->nm; break;
     case 19: src = s->rate; need = 8 * s->nm; break;
+    case 20: src = s->xp_prev; need = 24 * s->nm; break;
+    case 21: src = s->x_prev; need = 24 * s->nn; break;
+    case 22: src = s->dF; need = 72 * s->nm; break;
     default: return ORC_ERR_ARG;
     }
     if (bytes != need) return ORC_ERR_ARG;
@@ -1027,11 +1030,22 @@ int orc_sim_set(orc_sim *s, int32_t field, const void *src, int64_t bytes)
     case 9: dst = s->ebar; need = 8 * s->nm; break;
     case 10: dst = s->T; need = 8 * s->nm; break;
     case 11: dst = s->lam; need = 24 * s->nm; break;
+    case 20: dst = s->xp_prev; need = 24 * s->nm; break;
+    case 21: dst = s->x_prev; need = 24 * s->nn; break;
+    case 22: dst = s->dF; need = 72 * s->nm; break;
     default: return ORC_ERR_ARG;
     }
     if (bytes != need) return ORC_ERR_ARG;
     memcpy(dst, src, (size_t)need);
     return ORC_OK;
+}
+
+/* the tool contact of one node (Sec. 4.2), for tests: x (in/out) is the node's position after
+ * the central-difference update, du its increment before contact, t_next the time of the new
+ * position */
+void orc_tool_contact(const orc_params *P, double t_next, const double *du, double *x)
+{
+    tool_contact(P, t_next, du, x);
 }
 
 /* recompute supports and shape functions from the current positions (after orc_sim_set) */
