@@ -26,8 +26,10 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "otm_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
 _lock = threading.Lock()
 _lib = None
+_lib_omp = None
 
 OK = 0
 ERR_ARG, ERR_OOM, ERR_LME_NOCONV, ERR_JACOBIAN = -1, -3, -4, -5
@@ -35,13 +37,16 @@ ERR_NONFINITE, ERR_RETURNMAP_NOCONV, ERR_CAPACITY = -6, -7, -8
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc: serial, -O2, no floating-point contraction."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".{os.getpid()}.tmp"
-        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-               "-o", tmp, _SRC, "-lm"]
-        subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB)
+    """Compile the oracle with gcc (-O2, no floating-point contraction) twice: serial
+    (liboracle.so, the reference) and with OpenMP over independent material points and nodes
+    (liboracle_omp.so: the same arithmetic per point, so the same results)."""
+    for lib_path, extra in ((_LIB, []), (_LIB_OMP, ["-fopenmp"])):
+        if force or not os.path.exists(lib_path) or os.path.getmtime(lib_path) < os.path.getmtime(_SRC):
+            tmp = lib_path + f".{os.getpid()}.tmp"
+            cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", *extra,
+                   "-o", tmp, _SRC, "-lm"]
+            subprocess.run(cmd, check=True)
+            os.replace(tmp, lib_path)
     return _LIB
 
 
@@ -73,61 +78,70 @@ _P = C.c_void_p
 _D = C.POINTER(C.c_double)
 
 
-def lib():
-    global _lib
+def lib(omp: bool = False):
+    """The serial oracle library, or (omp=True) its OpenMP build."""
+    global _lib, _lib_omp
     with _lock:
-        if _lib is None:
+        if (_lib_omp if omp else _lib) is None:
             build()
-            L = C.CDLL(_LIB)
-            L.orc_lme.restype = C.c_int
-            L.orc_lme.argtypes = [C.c_int64, _P, C.c_double, C.c_double, C.c_int32, _P, _P, _P, _P]
-            L.orc_return_map.restype = C.c_int
-            L.orc_return_map.argtypes = [_P, C.c_double, _P, _P, C.c_double, C.c_double, C.c_double,
-                                         _P, _P, _P, _P, _P, _P]
-            L.orc_search.restype = C.c_int64
-            L.orc_search.argtypes = [C.c_int64, _P, C.c_int64, _P, C.c_double, C.c_double, _P, _P,
-                                     C.c_int64]
-            L.orc_grid_info.restype = C.c_int
-            L.orc_grid_info.argtypes = [C.c_int64, _P, C.c_double, _P, _P]
-            L.orc_grid_cells.restype = C.c_int
-            L.orc_grid_cells.argtypes = [C.c_int64, _P, C.c_double, C.c_int64, _P, _P]
-            L.orc_kinematics.restype = None
-            L.orc_kinematics.argtypes = [C.c_int64, _P, _P, _P, _P, _P, _P, _P]
-            L.orc_sim_create.restype = _P
-            L.orc_sim_create.argtypes = [_P, C.c_int64, C.c_int64, _P, _P, _P, _P, _P, _P, _P]
-            L.orc_sim_destroy.restype = None
-            L.orc_sim_destroy.argtypes = [_P]
-            L.orc_sim_step.restype = C.c_int
-            L.orc_sim_step.argtypes = [_P]
-            L.orc_sim_counts.restype = None
-            L.orc_sim_counts.argtypes = [_P] + [_P] * 6
-            L.orc_sim_get.restype = C.c_int
-            L.orc_sim_get.argtypes = [_P, C.c_int32, _P, C.c_int64]
-            L.orc_sim_set.restype = C.c_int
-            L.orc_sim_set.argtypes = [_P, C.c_int32, _P, C.c_int64]
-            L.orc_sim_refresh.restype = C.c_int
-            L.orc_sim_refresh.argtypes = [_P]
-            L.orc_lme_backward.restype = C.c_int
-            L.orc_lme_backward.argtypes = [C.c_int64, _P, _P, _P, _P, C.c_double, _P, _P, _P]
-            L.orc_return_map_backward.restype = C.c_int
-            L.orc_return_map_backward.argtypes = [_P, C.c_double, _P, _P, C.c_double, C.c_double, C.c_double,
-                                                  _P, _P, C.c_double, C.c_double, _P, _P, _P, _P, _P, _P]
-            L.orc_sim_clone.restype = _P
-            L.orc_sim_clone.argtypes = [_P]
-            L.orc_adj_create.restype = _P
-            L.orc_adj_create.argtypes = [_P, _P]
-            L.orc_adj_destroy.restype = None
-            L.orc_adj_destroy.argtypes = [_P]
-            L.orc_adj_result.restype = None
-            L.orc_adj_result.argtypes = [_P, _P, _P]
-            L.orc_tool_contact.restype = None
-            L.orc_tool_contact.argtypes = [_P, C.c_double, _P, _P]
-            L.orc_adjoint_step.restype = C.c_int
-            L.orc_adjoint_step.argtypes = [_P, _P, _P]
-            assert L.orc_sizeof_params() == C.sizeof(Params)
-            assert L.orc_sizeof_material() == C.sizeof(Material)
-            _lib = L
-    return _lib
+            L = _bind(C.CDLL(_LIB_OMP if omp else _LIB))
+            if omp:
+                _lib_omp = L
+            else:
+                _lib = L
+    return _lib_omp if omp else _lib
+
+
+def _bind(L):
+    """ctypes signatures of the oracle's entry points."""
+    L.orc_lme.restype = C.c_int
+    L.orc_lme.argtypes = [C.c_int64, _P, C.c_double, C.c_double, C.c_int32, _P, _P, _P, _P]
+    L.orc_return_map.restype = C.c_int
+    L.orc_return_map.argtypes = [_P, C.c_double, _P, _P, C.c_double, C.c_double, C.c_double,
+                                 _P, _P, _P, _P, _P, _P]
+    L.orc_search.restype = C.c_int64
+    L.orc_search.argtypes = [C.c_int64, _P, C.c_int64, _P, C.c_double, C.c_double, _P, _P,
+                             C.c_int64]
+    L.orc_grid_info.restype = C.c_int
+    L.orc_grid_info.argtypes = [C.c_int64, _P, C.c_double, _P, _P]
+    L.orc_grid_cells.restype = C.c_int
+    L.orc_grid_cells.argtypes = [C.c_int64, _P, C.c_double, C.c_int64, _P, _P]
+    L.orc_kinematics.restype = None
+    L.orc_kinematics.argtypes = [C.c_int64, _P, _P, _P, _P, _P, _P, _P]
+    L.orc_sim_create.restype = _P
+    L.orc_sim_create.argtypes = [_P, C.c_int64, C.c_int64, _P, _P, _P, _P, _P, _P, _P]
+    L.orc_sim_destroy.restype = None
+    L.orc_sim_destroy.argtypes = [_P]
+    L.orc_sim_step.restype = C.c_int
+    L.orc_sim_step.argtypes = [_P]
+    L.orc_sim_counts.restype = None
+    L.orc_sim_counts.argtypes = [_P] + [_P] * 6
+    L.orc_sim_get.restype = C.c_int
+    L.orc_sim_get.argtypes = [_P, C.c_int32, _P, C.c_int64]
+    L.orc_sim_set.restype = C.c_int
+    L.orc_sim_set.argtypes = [_P, C.c_int32, _P, C.c_int64]
+    L.orc_sim_refresh.restype = C.c_int
+    L.orc_sim_refresh.argtypes = [_P]
+    L.orc_lme_backward.restype = C.c_int
+    L.orc_lme_backward.argtypes = [C.c_int64, _P, _P, _P, _P, C.c_double, _P, _P, _P]
+    L.orc_return_map_backward.restype = C.c_int
+    L.orc_return_map_backward.argtypes = [_P, C.c_double, _P, _P, C.c_double, C.c_double, C.c_double,
+                                          _P, _P, C.c_double, C.c_double, _P, _P, _P, _P, _P, _P]
+    L.orc_sim_clone.restype = _P
+    L.orc_sim_clone.argtypes = [_P]
+    L.orc_adj_create.restype = _P
+    L.orc_adj_create.argtypes = [_P, _P]
+    L.orc_adj_destroy.restype = None
+    L.orc_adj_destroy.argtypes = [_P]
+    L.orc_adj_result.restype = None
+    L.orc_adj_result.argtypes = [_P, _P, _P]
+    L.orc_tool_contact.restype = None
+    L.orc_tool_contact.argtypes = [_P, C.c_double, _P, _P]
+    L.orc_adjoint_step.restype = C.c_int
+    L.orc_adjoint_step.argtypes = [_P, _P, _P]
+    assert L.orc_sizeof_params() == C.sizeof(Params)
+    assert L.orc_sizeof_material() == C.sizeof(Material)
+    return L
 
 
 def _ptr(a: np.ndarray):
@@ -300,8 +314,9 @@ FIELDS = dict(node_x=(0, 3, np.float64), node_du=(1, 3, np.float64), node_mass=(
 class Sim:
     """The oracle's whole explicit OTM simulation (Algorithm 1) on a scenarios.Problem."""
 
-    def __init__(self, prob, params: Params | None = None):
-        L = lib()
+    def __init__(self, prob, params: Params | None = None, omp: bool = False):
+        """omp=True runs the OpenMP build (same results, all host cores)."""
+        self._L = L = lib(omp)
         self.prob = prob
         self.params = params if params is not None else params_struct(prob)
         a = [np.ascontiguousarray(v) for v in (
@@ -315,18 +330,18 @@ class Sim:
 
     def __del__(self):
         if getattr(self, "_h", None):
-            lib().orc_sim_destroy(self._h)
+            self._L.orc_sim_destroy(self._h)
             self._h = None
 
     def counts(self):
         v = [C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64(), C.c_int32(), C.c_int64()]
-        lib().orc_sim_counts(self._h, *[C.byref(x) for x in v])
+        self._L.orc_sim_counts(self._h, *[C.byref(x) for x in v])
         return dict(n_nodes=v[0].value, n_mps=v[1].value, n_pairs=v[2].value, step=v[3].value,
                     err=v[4].value, err_id=v[5].value)
 
     def step(self, n: int = 1) -> int:
         for _ in range(n):
-            st = lib().orc_sim_step(self._h)
+            st = self._L.orc_sim_step(self._h)
             if st != OK:
                 return st
         return OK
@@ -343,7 +358,7 @@ class Sim:
         else:
             rows = c["n_mps"]
         out = np.zeros((rows, width) if width > 1 else (rows,), dtype=dt)
-        st = lib().orc_sim_get(self._h, code, _ptr(out), out.nbytes)
+        st = self._L.orc_sim_get(self._h, code, _ptr(out), out.nbytes)
         if st != OK:
             raise RuntimeError(f"get {name}: {st}")
         return out
@@ -351,17 +366,17 @@ class Sim:
     def set(self, name: str, value: np.ndarray):
         code, width, dt = FIELDS[name]
         v = np.ascontiguousarray(value, dtype=dt)
-        st = lib().orc_sim_set(self._h, code, _ptr(v), v.nbytes)
+        st = self._L.orc_sim_set(self._h, code, _ptr(v), v.nbytes)
         if st != OK:
             raise RuntimeError(f"set {name}: {st}")
 
     def refresh(self) -> int:
-        return lib().orc_sim_refresh(self._h)
+        return self._L.orc_sim_refresh(self._h)
 
     def clone(self) -> "Sim":
         c = Sim.__new__(Sim)
-        c.prob, c.params = self.prob, self.params
-        c._h = lib().orc_sim_clone(self._h)
+        c.prob, c.params, c._L = self.prob, self.params, self._L
+        c._h = self._L.orc_sim_clone(self._h)
         if not c._h:
             raise MemoryError("oracle clone failed")
         return c

@@ -612,61 +612,102 @@ static int sim_reserve_pairs(orc_sim *s, int64_t need)
     return ORC_OK;
 }
 
+/* the error with the smallest offending ID is kept (one writer at a time in the OpenMP build) */
 static void set_err(orc_sim *s, int code, int64_t id)
 {
-    if (s->err == ORC_OK || id < s->err_id) { s->err = code; s->err_id = id; }
+#pragma omp critical(orc_err)
+    {
+        if (s->err == ORC_OK || id < s->err_id) { s->err = code; s->err_id = id; }
+    }
 }
 
 /* Steps 5 and 6 of Algorithm 1 for every MP: linked-cell search at the current positions,
  * then the LME Newton solve warm-started from the MP's previous lambda. With lme_fail given, an
  * MP whose Newton solve fails is flagged there (its lambda keeps the warm start) instead of
- * stopping the step; every other error still stops it. */
+ * stopping the step; every other error stops it (the smallest offending ID is reported).
+ * The MPs are independent: a first pass counts each support, the counts give the CSR offsets,
+ * and a second pass searches again into the MP's own slice of the pair arrays and solves for
+ * its shape functions (in the OpenMP build both passes run over MPs in parallel). */
 static int search_and_shape(orc_sim *s, uint8_t *lme_fail)
 {
     const orc_params *P = &s->P;
+    const int64_t nm = s->nm;
     orc_grid g;
     int st = grid_build(&g, s->nn, s->x, P->cell_size);
     if (st != ORC_OK) return st;
-    int64_t cap_mp = 4096;
-    int32_t *buf = malloc((size_t)cap_mp * sizeof(int32_t));
-    double *d = malloc((size_t)cap_mp * 3 * sizeof(double));
-    if (!buf || !d) { free(buf); free(d); grid_free(&g); return ORC_ERR_OOM; }
-    s->off = xrealloc(s->off, (size_t)(s->nm + 1) * sizeof(int64_t));
-    s->off[0] = 0;
-    st = ORC_OK;
-    for (int64_t p = 0; p < s->nm && st == ORC_OK; p++) {
-        int64_t cnt = search_mp(&g, s->x, s->xp + 3 * p, P->rs2, P->cell_size, buf, cap_mp);
-        if (cnt > cap_mp) { st = ORC_ERR_CAPACITY; set_err(s, st, s->mp_gid[p]); break; }
-        int64_t base = s->off[p];
-        if ((st = sim_reserve_pairs(s, base + cnt)) != ORC_OK) break;
-        memcpy(s->ids + base, buf, (size_t)cnt * sizeof(int32_t));
-        s->off[p + 1] = base + cnt;
-        for (int64_t k = 0; k < cnt; k++)
-            for (int i = 0; i < 3; i++) d[3 * k + i] = s->xp[3 * p + i] - s->x[3 * (int64_t)buf[k] + i];
-        int32_t it = 0, it2 = 0;
-        double lam0[3] = {s->lam[3 * p], s->lam[3 * p + 1], s->lam[3 * p + 2]};
-        int lst = orc_lme(cnt, d, P->beta, P->newton_tol * P->h, P->max_newton, s->lam + 3 * p,
-                          s->N + base, s->dN + 3 * base, &it);
-        if (lst == ORC_ERR_LME_NOCONV && (lam0[0] != 0.0 || lam0[1] != 0.0 || lam0[2] != 0.0)) {
-            /* a warm start far from the solution can concentrate the weights on a node or two
-             * (singular Hessian): solve once more from lambda = 0 */
-            s->lam[3 * p] = s->lam[3 * p + 1] = s->lam[3 * p + 2] = 0.0;
-            lst = orc_lme(cnt, d, P->beta, P->newton_tol * P->h, P->max_newton, s->lam + 3 * p,
-                          s->N + base, s->dN + 3 * base, &it2);
-            it += it2;
+    const int64_t cap_mp = 4096;
+    int64_t *cnt = malloc((size_t)(nm + 1) * sizeof(int64_t));
+    s->off = xrealloc(s->off, (size_t)(nm + 1) * sizeof(int64_t));
+    if (!cnt || !s->off) { free(cnt); grid_free(&g); return ORC_ERR_OOM; }
+    int oom = 0;
+#pragma omp parallel
+    {
+        int32_t *buf = malloc((size_t)cap_mp * sizeof(int32_t));
+        if (!buf) {
+#pragma omp atomic write
+            oom = 1;
         }
-        s->newton_it[p] = it;
-        if (lst == ORC_ERR_LME_NOCONV && lme_fail && cnt > 0) {
-            lme_fail[p] = 1;
-            memcpy(s->lam + 3 * p, lam0, sizeof(lam0));
-        } else if (lst != ORC_OK) {
-            st = lst;
-            set_err(s, st, s->mp_gid[p]);
-        }
+#pragma omp for schedule(dynamic, 64)
+        for (int64_t p = 0; p < nm; p++)
+            cnt[p] = buf ? search_mp(&g, s->x, s->xp + 3 * p, P->rs2, P->cell_size, buf, cap_mp) : 0;
+        free(buf);
     }
-    if (st == ORC_OK) s->n_pairs = s->off[s->nm];
-    free(buf); free(d); grid_free(&g);
-    return st;
+    if (oom) { free(cnt); grid_free(&g); return ORC_ERR_OOM; }
+    s->off[0] = 0;
+    for (int64_t p = 0; p < nm; p++) {
+        if (cnt[p] > cap_mp) {
+            set_err(s, ORC_ERR_CAPACITY, s->mp_gid[p]);
+            free(cnt); grid_free(&g);
+            return ORC_ERR_CAPACITY;
+        }
+        s->off[p + 1] = s->off[p] + cnt[p];
+    }
+    free(cnt);
+    if ((st = sim_reserve_pairs(s, s->off[nm])) != ORC_OK) { grid_free(&g); return st; }
+    int failed = 0;
+#pragma omp parallel
+    {
+        double *d = malloc((size_t)cap_mp * 3 * sizeof(double));
+        if (!d) {
+#pragma omp atomic write
+            oom = 1;
+        }
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t p = 0; p < nm; p++) {
+            if (!d) continue;
+            const int64_t base = s->off[p], n = s->off[p + 1] - base;
+            search_mp(&g, s->x, s->xp + 3 * p, P->rs2, P->cell_size, s->ids + base, n);
+            for (int64_t k = 0; k < n; k++)
+                for (int i = 0; i < 3; i++) d[3 * k + i] = s->xp[3 * p + i] - s->x[3 * (int64_t)s->ids[base + k] + i];
+            int32_t it = 0, it2 = 0;
+            double lam0[3] = {s->lam[3 * p], s->lam[3 * p + 1], s->lam[3 * p + 2]};
+            int lst = orc_lme(n, d, P->beta, P->newton_tol * P->h, P->max_newton, s->lam + 3 * p,
+                              s->N + base, s->dN + 3 * base, &it);
+            if (lst == ORC_ERR_LME_NOCONV && (lam0[0] != 0.0 || lam0[1] != 0.0 || lam0[2] != 0.0)) {
+                /* a warm start far from the solution can concentrate the weights on a node or two
+                 * (singular Hessian): solve once more from lambda = 0 */
+                s->lam[3 * p] = s->lam[3 * p + 1] = s->lam[3 * p + 2] = 0.0;
+                lst = orc_lme(n, d, P->beta, P->newton_tol * P->h, P->max_newton, s->lam + 3 * p,
+                              s->N + base, s->dN + 3 * base, &it2);
+                it += it2;
+            }
+            s->newton_it[p] = it;
+            if (lst == ORC_ERR_LME_NOCONV && lme_fail && n > 0) {
+                lme_fail[p] = 1;
+                memcpy(s->lam + 3 * p, lam0, sizeof(lam0));
+            } else if (lst != ORC_OK) {
+                set_err(s, lst, s->mp_gid[p]);
+#pragma omp atomic write
+                failed = 1;
+            }
+        }
+        free(d);
+    }
+    grid_free(&g);
+    if (oom) return ORC_ERR_OOM;
+    if (failed) return s->err;
+    s->n_pairs = s->off[nm];
+    return ORC_OK;
 }
 
 /* ------------------------------------------------------------------ public: create */
@@ -876,6 +917,7 @@ int orc_sim_step(orc_sim *s)
     /* Step 2 (Eq. 4, Eq. 6): du_{n+1} = du_n + dt^2 r_I / m_I (nodes without mass keep du),
      * fixed nodes du = 0, rigid contact, x_{n+1} = x_n + du_{n+1}. */
     double t_next = s->time + dt;
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < nn; i++) {
         double *du = s->du + 3 * i, *x = s->x + 3 * i;
         double xn[3] = {x[0], x[1], x[2]};
@@ -901,6 +943,7 @@ int orc_sim_step(orc_sim *s)
     /* Step 3 (Eq. 9-13): x_p = sum N_I x_I,n+1; dF = 1 + sum du_I (x) grad N_I;
      * F_{n+1} = dF F_n; v_{n+1} = det(dF) v_n. Step 4: constitutive update. */
     int any_failed = 0;
+#pragma omp parallel for schedule(dynamic, 256) reduction(| : any_failed)
     for (int64_t p = 0; p < nm; p++) {
         double xpn[3] = {0, 0, 0}, D[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
         for (int64_t k = s->off[p]; k < s->off[p + 1]; k++) {

@@ -400,7 +400,7 @@ constexpr int kLmeWarps = 4;
 // convergence test, J'^-1, the next Newton step). FP64 instructions cost the pipe the same with
 // one active lane as with 32, so doing the scalar work once per MP instead of once per lane of
 // a warp saves most of it. State of one MP's solve, in shared memory:
-enum : int { kNewtonIdle = 0, kNewtonEval = 1, kNewtonDone = 2, kNewtonFail = 3 };
+enum : int { kNewtonIdle = 0, kNewtonEval = 1, kNewtonDone = 2, kNewtonFail = 3, kNewtonHessian = 4 };
 struct MpNewton {
     double E[11];      // sums of the latest evaluation: Z, r (3), A (6), shift
     double C[11];      // sums at the current (accepted) point
@@ -416,6 +416,7 @@ struct MpNewton {
     double qs;         // (solve's first shift - sh) * 1024/ln2, added to the stored prior terms
     double shift0;     // the solve's first shift (the stored prior terms are relative to it)
     int state, have_cur, iters, iters_total, halvings, retried;
+    int c_f32;         // the Hessian sums of C are the FP32 ones of a start's first evaluation
 };
 
 // the scaled trial and the shift of the pending evaluation: trials share the current point's
@@ -430,44 +431,91 @@ __device__ __forceinline__ void newton_set_trial(MpNewton &m)
 // One evaluation of the block path (Eq. 14 sums at the pending trial of MP state m): weights
 // into W.w, the sums into m.E (written by one lane per value), m.E[10] = the shift used. If Z
 // over- or underflows, again with the shift at the largest exponent. Warp-uniform.
-template <bool SHIFTED>
+//
+// The first evaluation of a start (F32H) accumulates the Hessian sums A = sum w d d^T in FP32:
+// from a warm start that evaluation only supplies the Newton step, whose accuracy needs the
+// residual r = sum w d exactly (it is a cancelling sum, kept in FP64) but the Hessian only to a
+// few digits (an error delta in J changes the next residual by about delta |r|). Where it is
+// also the last evaluation (the start already meets the tolerance), the FP64 Hessian is formed
+// from the stored weights by lme_hessian_block with the same per-lane order and warp tree, so
+// its sums are bit-identical to an FP64 evaluation's. Z and r use one formula in both modes.
+template <bool SHIFTED, bool F32H>
 __device__ __forceinline__ void lme_acc10(const WarpSmem &W, int n, double s0, double s1, double s2, double qs,
                                           int lane, const double *T, double (&v)[10])
 {
 #pragma unroll
     for (int i = 0; i < 10; i++) v[i] = 0.0;
+    float a[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (int k = lane; k < n; k += kWarp) {
         const double x = W.dx[k], y = W.dy[k], z = W.dz[k];
         const double qk = SHIFTED ? W.q[k] + qs : W.q[k];
         const double wk = exp_scaled(fma(s2, z, fma(s1, y, fma(s0, x, qk))), T);
         W.w[k] = wk;
-        const double wx = wk * x, wy = wk * y, wz = wk * z;
         v[0] += wk;
-        v[1] += wx; v[2] += wy; v[3] += wz;
-        v[4] = fma(wx, x, v[4]); v[5] = fma(wy, y, v[5]); v[6] = fma(wz, z, v[6]);
-        v[7] = fma(wx, y, v[7]); v[8] = fma(wy, z, v[8]); v[9] = fma(wx, z, v[9]);
+        v[1] = fma(wk, x, v[1]); v[2] = fma(wk, y, v[2]); v[3] = fma(wk, z, v[3]);
+        if (F32H) {
+            const float wf = (float)wk, xf = (float)x, yf = (float)y, zf = (float)z;
+            const float wxf = wf * xf, wyf = wf * yf, wzf = wf * zf;
+            a[0] = fmaf(wxf, xf, a[0]); a[1] = fmaf(wyf, yf, a[1]); a[2] = fmaf(wzf, zf, a[2]);
+            a[3] = fmaf(wxf, yf, a[3]); a[4] = fmaf(wyf, zf, a[4]); a[5] = fmaf(wxf, zf, a[5]);
+        } else {
+            const double wx = wk * x, wy = wk * y, wz = wk * z;
+            v[4] = fma(wx, x, v[4]); v[5] = fma(wy, y, v[5]); v[6] = fma(wz, z, v[6]);
+            v[7] = fma(wx, y, v[7]); v[8] = fma(wy, z, v[8]); v[9] = fma(wx, z, v[9]);
+        }
     }
+    if (F32H) {
+#pragma unroll
+        for (int i = 0; i < 6; i++) v[4 + i] = (double)a[i];
+    }
+}
+
+template <bool F32H>
+__device__ __forceinline__ double lme_sums10(const WarpSmem &W, int n, double s0, double s1, double s2, double qs,
+                                             int lane, const double *T)
+{
+    double v[10];
+    if (qs == 0.0) lme_acc10<false, F32H>(W, n, s0, s1, s2, qs, lane, T, v);
+    else lme_acc10<true, F32H>(W, n, s0, s1, s2, qs, lane, T, v);
+    return warp_reduce_scatter10(v, lane);
 }
 
 __device__ void lme_eval_block(const WarpSmem &W, int n, MpNewton &m, int lane, const double *T)
 {
     const double s0 = m.ts[0], s1 = m.ts[1], s2 = m.ts[2];
     double qs = m.qs, sh = m.sh;
-    double v[10];
-    if (qs == 0.0) lme_acc10<false>(W, n, s0, s1, s2, qs, lane, T, v);
-    else lme_acc10<true>(W, n, s0, s1, s2, qs, lane, T, v);
-    double t = warp_reduce_scatter10(v, lane);
+    const bool f32h = !m.have_cur;   // the first evaluation of a start
+    double t = f32h ? lme_sums10<true>(W, n, s0, s1, s2, qs, lane, T) : lme_sums10<false>(W, n, s0, s1, s2, qs, lane, T);
     const double Z = __shfl_sync(0xffffffffu, t, 0);
     if (!(Z > 1e-200) || !(Z < 1e200)) {
         double mx = -INFINITY;
         for (int k = lane; k < n; k += kWarp) mx = fmax(mx, W.q[k] + (s0 * W.dx[k] + s1 * W.dy[k] + s2 * W.dz[k]));
         sh = warp_max(mx) * (1.0 / kExpScale) + m.shift0;
         qs = (m.shift0 - sh) * kExpScale;
-        lme_acc10<true>(W, n, s0, s1, s2, qs, lane, T, v);
-        t = warp_reduce_scatter10(v, lane);
+        t = f32h ? lme_sums10<true>(W, n, s0, s1, s2, qs, lane, T) : lme_sums10<false>(W, n, s0, s1, s2, qs, lane, T);
     }
     if (rs10_writer(lane)) m.E[rs10_value(lane)] = t;
     if (lane == 0) m.E[10] = sh;
+}
+
+// The FP64 Hessian sums of the accepted point from its stored weights (for a start that met the
+// tolerance at its first, FP32-Hessian evaluation): the per-lane partials and the warp tree are
+// those of lme_acc10's FP64 branch, so the sums are bit-identical to an FP64 evaluation.
+__device__ void lme_hessian_block(const WarpSmem &W, int n, MpNewton &m, int lane)
+{
+    double v[10];
+#pragma unroll
+    for (int i = 0; i < 10; i++) v[i] = 0.0;
+    for (int k = lane; k < n; k += kWarp) {
+        const double x = W.dx[k], y = W.dy[k], z = W.dz[k];
+        const double wk = W.w[k];
+        const double wx = wk * x, wy = wk * y, wz = wk * z;
+        v[4] = fma(wx, x, v[4]); v[5] = fma(wy, y, v[5]); v[6] = fma(wz, z, v[6]);
+        v[7] = fma(wx, y, v[7]); v[8] = fma(wy, z, v[8]); v[9] = fma(wx, z, v[9]);
+    }
+    const double t = warp_reduce_scatter10(v, lane);
+    const int j = rs10_value(lane);
+    if (rs10_writer(lane) && j >= 4) m.C[j] = t;
 }
 
 __device__ __forceinline__ LmeSums sums_of(const double *v)
@@ -496,20 +544,45 @@ __device__ __forceinline__ void newton_fail(MpNewton &m)
     }
 }
 
+// the solve has converged at C (whose Hessian sums are FP64): J'^-1, 1/Z and the next shift for
+// the outputs
+__device__ __forceinline__ void newton_finish(MpNewton &m)
+{
+    const LmeSums c = sums_of(m.C);
+    double inv[6];
+    if (!lme_jinv(c, inv, &m.iZ)) {
+        newton_fail(m);
+        return;
+    }
+    for (int i = 0; i < 6; i++) m.inv[i] = inv[i];
+    // the next solve's shift only has to keep the weights near 1: log Z to within ln 2, from the
+    // binary exponent of Z (Z > 0 and finite here)
+    const int ez = ((__double2hiint(c.Z) >> 20) & 0x7ff) - 1023;
+    m.logz = fma((double)ez, 0x1.62e42fefa39efp-1, c.shift);
+    m.state = kNewtonDone;
+}
+
 // one scalar round after an evaluation (the damped Newton of lme_newton_loop, as a state machine)
 __device__ void newton_round(MpNewton &m, double tol, int max_it)
 {
+    if (m.state == kNewtonHessian) {  // the FP64 Hessian of the converged first evaluation is in C
+        m.c_f32 = 0;
+        newton_finish(m);
+        return;
+    }
     if (m.state != kNewtonEval) return;
     if (!m.have_cur) {               // the first evaluation of a start is the current point
         for (int i = 0; i < 11; i++) m.C[i] = m.E[i];
         for (int i = 0; i < 3; i++) m.lam[i] = m.trial[i];
         m.have_cur = 1;
+        m.c_f32 = 1;
     } else {                          // accept if log Z or the residual norm drops, else halve
         const LmeSums e = sums_of(m.E), c = sums_of(m.C);
         if (isfinite(e.Z) && (logz_less(e, c) || rn2(e) * (c.Z * c.Z) < rn2(c) * (e.Z * e.Z))) {
             for (int i = 0; i < 11; i++) m.C[i] = m.E[i];
             for (int i = 0; i < 3; i++) m.lam[i] = m.trial[i];
             m.halvings = 0;
+            m.c_f32 = 0;
         } else {
             if (++m.halvings >= 40) {
                 newton_fail(m);
@@ -528,17 +601,9 @@ __device__ void newton_round(MpNewton &m, double tol, int max_it)
         return;
     }
     double inv[6];
-    if (r2 <= tol * tol * c.Z * c.Z) {   // converged: J'^-1, 1/Z and the next shift for the outputs
-        if (!lme_jinv(c, inv, &m.iZ)) {
-            newton_fail(m);
-            return;
-        }
-        for (int i = 0; i < 6; i++) m.inv[i] = inv[i];
-        // the next solve's shift only has to keep the weights near 1: log Z to within ln 2,
-        // from the binary exponent of Z (Z > 0 and finite here)
-        const int ez = ((__double2hiint(c.Z) >> 20) & 0x7ff) - 1023;
-        m.logz = fma((double)ez, 0x1.62e42fefa39efp-1, c.shift);
-        m.state = kNewtonDone;
+    if (r2 <= tol * tol * c.Z * c.Z) {   // converged
+        if (m.c_f32) m.state = kNewtonHessian;   // the FP64 Hessian first (lme_hessian_block)
+        else newton_finish(m);
         return;
     }
     if (m.iters >= max_it || !lme_jinv(c, inv)) {
@@ -751,7 +816,7 @@ __global__ void __launch_bounds__(kLmeWarps * kWarp) k_lme(const Dev D)
             M.trial[1] = M.ws[1] = l1;
             M.trial[2] = M.ws[2] = l2;
             M.t = 1.0;
-            M.have_cur = M.iters = M.iters_total = M.halvings = M.retried = 0;
+            M.have_cur = M.iters = M.iters_total = M.halvings = M.retried = M.c_f32 = 0;
             M.shift0 = shift0;
             newton_set_trial(M);
             M.state = cnt > 0 ? kNewtonEval : kNewtonFail;
@@ -765,12 +830,15 @@ __global__ void __launch_bounds__(kLmeWarps * kWarp) k_lme(const Dev D)
         if (M.state == kNewtonEval) {
             __syncwarp();
             lme_eval_block(W, cnt, M, lane, T);
+        } else if (M.state == kNewtonHessian) {
+            __syncwarp();
+            lme_hessian_block(W, cnt, M, lane);
         }
         __syncthreads();
         bool pending = false;
         if (warp == 0 && lane < kLmeWarps) {
             newton_round(NS[lane], D.tol_abs, D.max_newton);
-            pending = NS[lane].state == kNewtonEval;
+            pending = NS[lane].state == kNewtonEval || NS[lane].state == kNewtonHessian;
         }
         if (!__syncthreads_or(pending)) break;
     }

@@ -290,3 +290,14 @@ def test_erosion_removes_exactly_the_failed_points_and_their_orphan_nodes(orc):
               if not np.any(((xp - p.node_x[i]) ** 2).sum(1) <= p.rs2)]
     assert len(orphan) > 0
     assert np.array_equal(sim.get("node_gid"), np.setdiff1d(np.arange(p.n_nodes), orphan))
+
+
+def test_openmp_build_gives_the_serial_results(orc):
+    """The OpenMP build of the oracle runs independent material points and nodes in parallel
+    with the same arithmetic per point: a trajectory through the impact is bit-identical."""
+    p = scenarios.taylor_rod(h=0.8e-3, R=3.2e-3, L=6.4e-3, material=scenarios.copper_jc(), v0=300.0)
+    a, b = orc.Sim(p), orc.Sim(p, omp=True)
+    assert a.step(12) == 0 and b.step(12) == 0
+    for f in ("node_x", "node_du", "node_mass", "node_force", "mp_x", "F", "sigma", "be", "ebar", "T", "lam",
+              "offsets", "ids", "N", "dN", "newton_it"):
+        assert np.array_equal(a.get(f), b.get(f)), f
