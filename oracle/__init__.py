@@ -135,6 +135,8 @@ def _bind(L):
     L.orc_adj_destroy.argtypes = [_P]
     L.orc_adj_result.restype = None
     L.orc_adj_result.argtypes = [_P, _P, _P]
+    L.orc_sim_row.restype = C.c_int64
+    L.orc_sim_row.argtypes = [_P, C.c_int64, _P, _P, _P, C.c_int64]
     L.orc_tool_contact.restype = None
     L.orc_tool_contact.argtypes = [_P, C.c_double, _P, _P]
     L.orc_adjoint_step.restype = C.c_int
@@ -362,6 +364,16 @@ class Sim:
         if st != OK:
             raise RuntimeError(f"get {name}: {st}")
         return out
+
+    def row(self, p: int, cap: int = 4096):
+        """MP p's support: (node IDs ascending, N, grad N)."""
+        ids = np.zeros(cap, np.int32)
+        N = np.zeros(cap)
+        dN = np.zeros((cap, 3))
+        n = self._L.orc_sim_row(self._h, int(p), _ptr(ids), _ptr(N), _ptr(dN), cap)
+        if n < 0:
+            raise IndexError(p)
+        return ids[:n].copy(), N[:n].copy(), dN[:n].copy()
 
     def set(self, name: str, value: np.ndarray):
         code, width, dt = FIELDS[name]

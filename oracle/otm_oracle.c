@@ -1083,6 +1083,19 @@ int orc_sim_set(orc_sim *s, int32_t field, const void *src, int64_t bytes)
     return ORC_OK;
 }
 
+/* one MP's support row: its node IDs (ascending), N and grad N; returns the row length, or -1 if
+ * p is out of range or the row is longer than cap (nothing copied) */
+int64_t orc_sim_row(const orc_sim *s, int64_t p, int32_t *ids, double *N, double *dN, int64_t cap)
+{
+    if (p < 0 || p >= s->nm) return -1;
+    const int64_t b = s->off[p], n = s->off[p + 1] - b;
+    if (n > cap) return -1;
+    memcpy(ids, s->ids + b, (size_t)n * sizeof(int32_t));
+    memcpy(N, s->N + b, (size_t)n * sizeof(double));
+    memcpy(dN, s->dN + 3 * b, (size_t)n * 3 * sizeof(double));
+    return n;
+}
+
 /* the tool contact of one node (Sec. 4.2), for tests: x (in/out) is the node's position after
  * the central-difference update, du its increment before contact, t_next the time of the new
  * position */

@@ -15,6 +15,15 @@ namespace otm {
 
 constexpr int kAdjWarps = 4;
 
+// (N, grad N) of a stored pair row (N, e = N d): grad N = -K e with K = J^-1 of the MP's LME
+// solve (xx, yy, zz, xy, yz, xz)
+__device__ __forceinline__ double4_32a grad_row(const double4_32a r, double k0, double k1, double k2, double k3,
+                                                double k4, double k5)
+{
+    return make_double4_32a(r.x, -(k0 * r.y + k3 * r.z + k5 * r.w), -(k3 * r.y + k1 * r.z + k4 * r.w),
+                            -(k5 * r.y + k4 * r.z + k2 * r.w));
+}
+
 // ---------------------------------------------------------------------------- LME backward
 // d_a = x_p - x_a, N = softmax(f), f_a = -beta |d_a|^2 + lambda . d_a, lambda from
 // r = sum N d = 0, grad N_a = -N_a H^-1 d_a, H = sum N d d^T - r r^T.
@@ -393,9 +402,11 @@ __global__ void __launch_bounds__(kAdjWarps * kWarp) k_adj_kin(const Dev D, cons
     double Db[9];
     for (int i = 0; i < 9; i++) Db[i] = A.dFb[9 * p + i];
     const double4_32a xpb = A.xpb[p];
+    const double *K = A.K_n + 6 * p;
+    const double k0 = K[0], k1 = K[1], k2 = K[2], k3 = K[3], k4 = K[4], k5 = K[5];
     for (int k = lane; k < n; k += kWarp) {
         const int id = A.ids_n[base + k];
-        const double4_32a sh = A.shape_n[base + k];
+        const double4_32a sh = grad_row(A.shape_n[base + k], k0, k1, k2, k3, k4, k5);
         const double4_32a u = D.du[id], xa = D.x[id];
         const double ub0 = Db[0] * sh.y + Db[1] * sh.z + Db[2] * sh.w;
         const double ub1 = Db[3] * sh.y + Db[4] * sh.z + Db[5] * sh.w;
@@ -483,12 +494,14 @@ __global__ void __launch_bounds__(kAdjWarps * kWarp) k_adj_force(const Dev D, co
     const double *sg = A.sig_n + 6 * p;
     const double sxx = sg[0], syy = sg[1], szz = sg[2], sxy = sg[3], syz = sg[4], sxz = sg[5];
     const double vp = A.vol_n[p], mp = D.mass[p];
+    const double *K = A.K_n + 6 * p;
+    const double k0 = K[0], k1 = K[1], k2 = K[2], k3 = K[3], k4 = K[4], k5 = K[5];
     double v[16];
 #pragma unroll
     for (int k = 0; k < 16; k++) v[k] = 0.0;
     for (int k = lane; k < n; k += kWarp) {
         const int id = A.ids_n[base + k];
-        const double4_32a sh = A.shape_n[base + k];
+        const double4_32a sh = grad_row(A.shape_n[base + k], k0, k1, k2, k3, k4, k5);
         const double4_32a rb = A.rb[id];
         double4_32a pb = A.pb_prev[base + k];
         pb.x += rb.w * mp;

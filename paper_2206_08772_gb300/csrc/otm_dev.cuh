@@ -5,7 +5,7 @@
 //            flags, influence counts, node-major offsets, linked-cell arrays
 //   MPs    : x_p (double4_32a), F, dF (9), b^e, sigma (6), vol, mass, ebar, T, rate, J, lambda (3),
 //            material, support count, Newton iterations, failure flag, original ID
-//   pairs  : padded MP-major rows of S slots: node ID (int32), shape (double4_32a: N, grad N),
+//   pairs  : padded MP-major rows of S slots: node ID (int32), shape (double4_32a: N, e = N d),
 //            rank in the node's influence list (uint16); node-major contributions
 //            (double4_32a or float4: m_p N, -v sigma grad N) at noff[node] + rank
 #pragma once
@@ -82,6 +82,7 @@ struct Dev {
     double *F, *dF, *be, *sig, *vol, *mass, *ebar, *T, *rate, *lam, *logz, *logz_in;
     double *lam_prev, *lam_prev2, *lam_prev3;   // lambda of the three steps before (start extrapolation)
     double *Qe;                      // eigenvectors of b^e from the last return map (9, row-major)
+    double *Kinv;                    // J^-1 of the last LME solve (6: xx, yy, zz, xy, yz, xz), see k_lme
     int32_t *mat_id, *cnt, *newton_it;
     uint8_t *failed;                 // fracture flags of the step
     uint8_t *lme_fail;               // LME failures of the step (node insertion)
@@ -121,8 +122,9 @@ struct AdjDev {
     // copies of state n taken before the step is recomputed
     double4_32a *du_n;
     double *F_n, *be_n, *ebar_n, *T_n, *vol_n, *sig_n;
-    double4_32a *shape_n;
-    double4_32a *shape_next;           // shape functions of state n+1 kept from the previous backward step
+    double4_32a *shape_n;              // shape rows (N, N d) of state n
+    double4_32a *shape_next;           // shape rows of state n+1 kept from the previous backward step
+    double *K_n, *K_next;              // the matching J^-1 per MP (grad N_a = -J^-1 N_a d_a)
     int32_t *ids_n, *cnt_n, *noff_n;
     uint16_t *rank_n;
     // per-pair node contributions in node-major order

@@ -24,7 +24,7 @@ namespace otm {
 // exponential function in IEEE floating-point arithmetic", ACM TOMS 15(2), 1989), with the
 // argument scaling folded into the caller: the argument arrives as y = f * 1024 / ln 2 (the LME
 // scales lambda and the prior term instead of every exponent), and
-//   y = n + s, n = round(y) (the 1.5*2^52 shifter), |s| <= 1/2 and exact (Sterbenz),
+//   y = n + s, n = round(y), |s| <= 1/2 and exact (integer operations on y's bits, see below),
 //   exp(f) = 2^(n >> 10) * 2^((n & 1023) / 1024) * exp(s ln2 / 1024),
 // with exp(t) - 1 for |t| <= ln2/2048 by its Taylor polynomial of degree 3 (truncation below
 // 5.5e-16 relative). The 1024-entry table 2^(j/1024) is computed once on the host (C library
@@ -82,14 +82,46 @@ __device__ __forceinline__ void exp_table_load(double *T)
 
 __device__ __forceinline__ double exp_scaled(double y, const double *T)
 {
-    const double t = y + kExpShifter;
-    const int hi = __double2hiint(t);
-    const int n = __double2loint(t);
-    // the high word of t is 0x43380000 for round(y) in [0, 2^32) and 0x4337ffff for [-2^32, 0);
-    // a mismatch with the sign of the low word means |y| >= 2^31 (or y is not finite)
-    if (n < kExpNmin || n > kExpNmax || hi != (n < 0 ? 0x4337ffff : 0x43380000)) return (y > 0.0) ? INFINITY : 0.0;
-    const double nd = t - kExpShifter;
-    const double sr = y - nd;
+    // y = n + s with n = round(y) and s exact, |s| <= 1/2. For 1 <= |y| < 2^20 (every weight of the
+    // LME sums: y <= 0, and |y| < 1 only for a single node that carries nearly all the weight)
+    // n and s are formed from y's bits with integer operations, which leaves the FP64 pipe to the
+    // polynomial; other arguments take the 1.5 * 2^52 shifter (three FP64 additions).
+    const int hi = __double2hiint(y);
+    const int E = ((hi >> 20) & 0x7ff) - 1023;
+    int n;
+    double sr;
+    if (E >= 0 && E < 20) {
+        // significand M (53 bits) = |y| 2^(52 - E); f = 52 - E fraction bits (33..52)
+        const unsigned long long M =
+            ((unsigned long long)((hi & 0xfffff) | 0x100000) << 32) | (unsigned)__double2loint(y);
+        const int f = 52 - E;
+        const unsigned long long na = (M + (1ULL << (f - 1))) >> f;   // |n|, rounded half up
+        const long long rem = (long long)(M - (na << f));             // |rem| <= 2^(f-1) < 2^52
+        const bool neg = hi < 0;
+        n = neg ? -(int)na : (int)na;
+        // s = rem 2^-f (sign of y applied): normalised with integer operations, exactly (|rem| has
+        // at most 52 significant bits, so the 12 or more leading zeros cover the 11 dropped bits)
+        const unsigned long long a = (unsigned long long)(rem < 0 ? -rem : rem);
+        if (a == 0) {
+            sr = 0.0;
+        } else {
+            const int lz = __clzll((long long)a);
+            const unsigned long long m = (a << lz) >> 11;          // 1.xxx in bits 52..0
+            const long long ex = 1023 + 63 - lz - f;
+            const bool sneg = (rem < 0) != neg;
+            sr = __longlong_as_double((long long)((sneg ? 0x8000000000000000ULL : 0ULL) |
+                                                  ((unsigned long long)ex << 52) | (m & 0xFFFFFFFFFFFFFULL)));
+        }
+    } else {
+        const double t = y + kExpShifter;
+        const int thi = __double2hiint(t);
+        n = __double2loint(t);
+        // the high word of t is 0x43380000 for round(y) in [0, 2^32) and 0x4337ffff for
+        // [-2^32, 0); a mismatch with the sign of the low word means |y| >= 2^31 (or y is not finite)
+        if (thi != (n < 0 ? 0x4337ffff : 0x43380000)) return (y > 0.0) ? INFINITY : 0.0;
+        sr = y - (t - kExpShifter);
+    }
+    if (n < kExpNmin || n > kExpNmax) return (y > 0.0) ? INFINITY : 0.0;
     const double p = sr * fma(sr, fma(sr, kExpC3, kExpC2), kExpC1);
     const double Tj = T[n & (kExpTable - 1)];
     const double v = fma(Tj, p, Tj);
@@ -400,7 +432,7 @@ constexpr int kLmeWarps = 4;
 // convergence test, J'^-1, the next Newton step). FP64 instructions cost the pipe the same with
 // one active lane as with 32, so doing the scalar work once per MP instead of once per lane of
 // a warp saves most of it. State of one MP's solve, in shared memory:
-enum : int { kNewtonIdle = 0, kNewtonEval = 1, kNewtonDone = 2, kNewtonFail = 3, kNewtonHessian = 4 };
+enum : int { kNewtonIdle = 0, kNewtonEval = 1, kNewtonDone = 2, kNewtonFail = 3 };
 struct MpNewton {
     double E[11];      // sums of the latest evaluation: Z, r (3), A (6), shift
     double C[11];      // sums at the current (accepted) point
@@ -416,7 +448,6 @@ struct MpNewton {
     double qs;         // (solve's first shift - sh) * 1024/ln2, added to the stored prior terms
     double shift0;     // the solve's first shift (the stored prior terms are relative to it)
     int state, have_cur, iters, iters_total, halvings, retried;
-    int c_f32;         // the Hessian sums of C are the FP32 ones of a start's first evaluation
 };
 
 // the scaled trial and the shift of the pending evaluation: trials share the current point's
@@ -431,91 +462,44 @@ __device__ __forceinline__ void newton_set_trial(MpNewton &m)
 // One evaluation of the block path (Eq. 14 sums at the pending trial of MP state m): weights
 // into W.w, the sums into m.E (written by one lane per value), m.E[10] = the shift used. If Z
 // over- or underflows, again with the shift at the largest exponent. Warp-uniform.
-//
-// The first evaluation of a start (F32H) accumulates the Hessian sums A = sum w d d^T in FP32:
-// from a warm start that evaluation only supplies the Newton step, whose accuracy needs the
-// residual r = sum w d exactly (it is a cancelling sum, kept in FP64) but the Hessian only to a
-// few digits (an error delta in J changes the next residual by about delta |r|). Where it is
-// also the last evaluation (the start already meets the tolerance), the FP64 Hessian is formed
-// from the stored weights by lme_hessian_block with the same per-lane order and warp tree, so
-// its sums are bit-identical to an FP64 evaluation's. Z and r use one formula in both modes.
-template <bool SHIFTED, bool F32H>
+template <bool SHIFTED>
 __device__ __forceinline__ void lme_acc10(const WarpSmem &W, int n, double s0, double s1, double s2, double qs,
                                           int lane, const double *T, double (&v)[10])
 {
 #pragma unroll
     for (int i = 0; i < 10; i++) v[i] = 0.0;
-    float a[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (int k = lane; k < n; k += kWarp) {
         const double x = W.dx[k], y = W.dy[k], z = W.dz[k];
         const double qk = SHIFTED ? W.q[k] + qs : W.q[k];
         const double wk = exp_scaled(fma(s2, z, fma(s1, y, fma(s0, x, qk))), T);
         W.w[k] = wk;
+        const double wx = wk * x, wy = wk * y, wz = wk * z;
         v[0] += wk;
-        v[1] = fma(wk, x, v[1]); v[2] = fma(wk, y, v[2]); v[3] = fma(wk, z, v[3]);
-        if (F32H) {
-            const float wf = (float)wk, xf = (float)x, yf = (float)y, zf = (float)z;
-            const float wxf = wf * xf, wyf = wf * yf, wzf = wf * zf;
-            a[0] = fmaf(wxf, xf, a[0]); a[1] = fmaf(wyf, yf, a[1]); a[2] = fmaf(wzf, zf, a[2]);
-            a[3] = fmaf(wxf, yf, a[3]); a[4] = fmaf(wyf, zf, a[4]); a[5] = fmaf(wxf, zf, a[5]);
-        } else {
-            const double wx = wk * x, wy = wk * y, wz = wk * z;
-            v[4] = fma(wx, x, v[4]); v[5] = fma(wy, y, v[5]); v[6] = fma(wz, z, v[6]);
-            v[7] = fma(wx, y, v[7]); v[8] = fma(wy, z, v[8]); v[9] = fma(wx, z, v[9]);
-        }
+        v[1] += wx; v[2] += wy; v[3] += wz;
+        v[4] = fma(wx, x, v[4]); v[5] = fma(wy, y, v[5]); v[6] = fma(wz, z, v[6]);
+        v[7] = fma(wx, y, v[7]); v[8] = fma(wy, z, v[8]); v[9] = fma(wx, z, v[9]);
     }
-    if (F32H) {
-#pragma unroll
-        for (int i = 0; i < 6; i++) v[4 + i] = (double)a[i];
-    }
-}
-
-template <bool F32H>
-__device__ __forceinline__ double lme_sums10(const WarpSmem &W, int n, double s0, double s1, double s2, double qs,
-                                             int lane, const double *T)
-{
-    double v[10];
-    if (qs == 0.0) lme_acc10<false, F32H>(W, n, s0, s1, s2, qs, lane, T, v);
-    else lme_acc10<true, F32H>(W, n, s0, s1, s2, qs, lane, T, v);
-    return warp_reduce_scatter10(v, lane);
 }
 
 __device__ void lme_eval_block(const WarpSmem &W, int n, MpNewton &m, int lane, const double *T)
 {
     const double s0 = m.ts[0], s1 = m.ts[1], s2 = m.ts[2];
     double qs = m.qs, sh = m.sh;
-    const bool f32h = !m.have_cur;   // the first evaluation of a start
-    double t = f32h ? lme_sums10<true>(W, n, s0, s1, s2, qs, lane, T) : lme_sums10<false>(W, n, s0, s1, s2, qs, lane, T);
+    double v[10];
+    if (qs == 0.0) lme_acc10<false>(W, n, s0, s1, s2, qs, lane, T, v);
+    else lme_acc10<true>(W, n, s0, s1, s2, qs, lane, T, v);
+    double t = warp_reduce_scatter10(v, lane);
     const double Z = __shfl_sync(0xffffffffu, t, 0);
     if (!(Z > 1e-200) || !(Z < 1e200)) {
         double mx = -INFINITY;
         for (int k = lane; k < n; k += kWarp) mx = fmax(mx, W.q[k] + (s0 * W.dx[k] + s1 * W.dy[k] + s2 * W.dz[k]));
         sh = warp_max(mx) * (1.0 / kExpScale) + m.shift0;
         qs = (m.shift0 - sh) * kExpScale;
-        t = f32h ? lme_sums10<true>(W, n, s0, s1, s2, qs, lane, T) : lme_sums10<false>(W, n, s0, s1, s2, qs, lane, T);
+        lme_acc10<true>(W, n, s0, s1, s2, qs, lane, T, v);
+        t = warp_reduce_scatter10(v, lane);
     }
     if (rs10_writer(lane)) m.E[rs10_value(lane)] = t;
     if (lane == 0) m.E[10] = sh;
-}
-
-// The FP64 Hessian sums of the accepted point from its stored weights (for a start that met the
-// tolerance at its first, FP32-Hessian evaluation): the per-lane partials and the warp tree are
-// those of lme_acc10's FP64 branch, so the sums are bit-identical to an FP64 evaluation.
-__device__ void lme_hessian_block(const WarpSmem &W, int n, MpNewton &m, int lane)
-{
-    double v[10];
-#pragma unroll
-    for (int i = 0; i < 10; i++) v[i] = 0.0;
-    for (int k = lane; k < n; k += kWarp) {
-        const double x = W.dx[k], y = W.dy[k], z = W.dz[k];
-        const double wk = W.w[k];
-        const double wx = wk * x, wy = wk * y, wz = wk * z;
-        v[4] = fma(wx, x, v[4]); v[5] = fma(wy, y, v[5]); v[6] = fma(wz, z, v[6]);
-        v[7] = fma(wx, y, v[7]); v[8] = fma(wy, z, v[8]); v[9] = fma(wx, z, v[9]);
-    }
-    const double t = warp_reduce_scatter10(v, lane);
-    const int j = rs10_value(lane);
-    if (rs10_writer(lane) && j >= 4) m.C[j] = t;
 }
 
 __device__ __forceinline__ LmeSums sums_of(const double *v)
@@ -565,24 +549,17 @@ __device__ __forceinline__ void newton_finish(MpNewton &m)
 // one scalar round after an evaluation (the damped Newton of lme_newton_loop, as a state machine)
 __device__ void newton_round(MpNewton &m, double tol, int max_it)
 {
-    if (m.state == kNewtonHessian) {  // the FP64 Hessian of the converged first evaluation is in C
-        m.c_f32 = 0;
-        newton_finish(m);
-        return;
-    }
     if (m.state != kNewtonEval) return;
     if (!m.have_cur) {               // the first evaluation of a start is the current point
         for (int i = 0; i < 11; i++) m.C[i] = m.E[i];
         for (int i = 0; i < 3; i++) m.lam[i] = m.trial[i];
         m.have_cur = 1;
-        m.c_f32 = 1;
     } else {                          // accept if log Z or the residual norm drops, else halve
         const LmeSums e = sums_of(m.E), c = sums_of(m.C);
         if (isfinite(e.Z) && (logz_less(e, c) || rn2(e) * (c.Z * c.Z) < rn2(c) * (e.Z * e.Z))) {
             for (int i = 0; i < 11; i++) m.C[i] = m.E[i];
             for (int i = 0; i < 3; i++) m.lam[i] = m.trial[i];
             m.halvings = 0;
-            m.c_f32 = 0;
         } else {
             if (++m.halvings >= 40) {
                 newton_fail(m);
@@ -602,8 +579,7 @@ __device__ void newton_round(MpNewton &m, double tol, int max_it)
     }
     double inv[6];
     if (r2 <= tol * tol * c.Z * c.Z) {   // converged
-        if (m.c_f32) m.state = kNewtonHessian;   // the FP64 Hessian first (lme_hessian_block)
-        else newton_finish(m);
+        newton_finish(m);
         return;
     }
     if (m.iters >= max_it || !lme_jinv(c, inv)) {
@@ -692,10 +668,7 @@ __global__ void __launch_bounds__(kSearchWarps * kWarp) k_kin_search(const Dev D
     }
     const double t = warp_reduce_scatter12(v, lane);
     const int j = rs12_value(lane);
-    if (rs12_writer(lane) && j >= 3) {
-        const int c = j - 3;
-        D.dF[9 * p + c] = (c == 0 || c == 4 || c == 8) ? 1.0 + t : t;
-    }
+    if (rs12_writer(lane) && j >= 3) D.dF[9 * p + (j - 3)] = t;   // G = sum du (x) e; k_return_map forms dF
     // values 0, 1, 2 (x_p) sit at lanes 0, 2, 4
     const double px = __shfl_sync(0xffffffffu, t, 0), py = __shfl_sync(0xffffffffu, t, 2),
                  pz = __shfl_sync(0xffffffffu, t, 4);
@@ -816,7 +789,7 @@ __global__ void __launch_bounds__(kLmeWarps * kWarp) k_lme(const Dev D)
             M.trial[1] = M.ws[1] = l1;
             M.trial[2] = M.ws[2] = l2;
             M.t = 1.0;
-            M.have_cur = M.iters = M.iters_total = M.halvings = M.retried = M.c_f32 = 0;
+            M.have_cur = M.iters = M.iters_total = M.halvings = M.retried = 0;
             M.shift0 = shift0;
             newton_set_trial(M);
             M.state = cnt > 0 ? kNewtonEval : kNewtonFail;
@@ -830,15 +803,12 @@ __global__ void __launch_bounds__(kLmeWarps * kWarp) k_lme(const Dev D)
         if (M.state == kNewtonEval) {
             __syncwarp();
             lme_eval_block(W, cnt, M, lane, T);
-        } else if (M.state == kNewtonHessian) {
-            __syncwarp();
-            lme_hessian_block(W, cnt, M, lane);
         }
         __syncthreads();
         bool pending = false;
         if (warp == 0 && lane < kLmeWarps) {
             newton_round(NS[lane], D.tol_abs, D.max_newton);
-            pending = NS[lane].state == kNewtonEval || NS[lane].state == kNewtonHessian;
+            pending = NS[lane].state == kNewtonEval;
         }
         if (!__syncthreads_or(pending)) break;
     }
@@ -862,16 +832,34 @@ __global__ void __launch_bounds__(kLmeWarps * kWarp) k_lme(const Dev D)
     const double iZ = M.iZ;
     if (st != OTM_OK) return;
 
-    // N_a = w_a / Z, grad N_a = -N_a J^-1 d_a = -w_a J'^-1 d_a; contributions for Eq. 5 of the next
-    // step, stored at the pair's place in its node's influence list
+    // N_a = w_a / Z and grad N_a = -N_a J^-1 d_a = -K e_a with e_a = N_a d_a and K = J^-1 = Z J'^-1
+    // (one symmetric 3x3 per MP). The pair rows keep (N_a, e_a) and the MP keeps K: whoever needs
+    // grad N applies K once per MP (the kinematics gather sums du_a (x) e_a, and dF = 1 - G K
+    // follows in the return map), so the per-pair work here is N, e and the contributions.
+    // Eq. 5 contributions of the next step, stored at the pair's place in its node's influence
+    // list: mass m_p N_a, force -v_p sigma_p grad N_a = (v_p sigma_p K) e_a = Q e_a.
     const double mp = D.mass[p], vp = D.vol[p];
     const double *sg = D.sig + 6 * p;
-    // -v_p sigma_p, so that the force contribution is one 3x3 product with grad N
-    const double sxx = -vp * sg[0], syy = -vp * sg[1], szz = -vp * sg[2], sxy = -vp * sg[3], syz = -vp * sg[4],
-                 sxz = -vp * sg[5];
+    double Kc[6], Q[9];
+    {
+        // lanes 0-5 form K (and store it), lanes 0-8 one entry of Q each; all lanes get both
+        const double Zc = M.C[0];
+        const double kj = (lane < 6) ? inv[lane] * Zc : 0.0;
+        if (lane < 6) D.Kinv[6 * p + lane] = kj;
+#pragma unroll
+        for (int i = 0; i < 6; i++) Kc[i] = __shfl_sync(0xffffffffu, kj, i);
+        // symmetric index of (i, j) in (xx, yy, zz, xy, yz, xz)
+        const int li = (lane < 9) ? lane / 3 : 0, lc = (lane < 9) ? lane % 3 : 0;
+        auto sym = [](int i, int j) { return i == j ? i : (i + j == 1 ? 3 : (i + j == 3 ? 4 : 5)); };
+        const double q = vp * (sg[sym(li, 0)] * Kc[sym(0, lc)] + sg[sym(li, 1)] * Kc[sym(1, lc)] +
+                               sg[sym(li, 2)] * Kc[sym(2, lc)]);
+#pragma unroll
+        for (int i = 0; i < 9; i++) Q[i] = __shfl_sync(0xffffffffu, q, i);
+    }
     int em = -2000, ef = -2000;   // largest binary exponents of the stored mass / force terms
-    const float fsxx = (float)sxx, fsyy = (float)syy, fszz = (float)szz, fsxy = (float)sxy, fsyz = (float)syz,
-                fsxz = (float)sxz;
+    float Qf[9];
+#pragma unroll
+    for (int i = 0; i < 9; i++) Qf[i] = MIXED ? (float)Q[i] : 0.f;
     // stabilisation (Eq. 7-8): -eps N_a e_a / |x_a,n-1 - x_p,n-1|,
     // e_a = x_a - x_p - dF (x_a,n-1 - x_p,n-1), with dF the increment that led to this state
     double xq0 = 0, xq1 = 0, xq2 = 0, F00 = 0, F01 = 0, F02 = 0, F10 = 0, F11 = 0, F12 = 0, F20 = 0, F21 = 0, F22 = 0;
@@ -886,10 +874,8 @@ __global__ void __launch_bounds__(kLmeWarps * kWarp) k_lme(const Dev D)
         const double wk = W.w[k];
         const double N = wk * iZ;
         const double x = W.dx[k], y = W.dy[k], z = W.dz[k];
-        const double gx = -wk * (inv[0] * x + inv[3] * y + inv[5] * z);
-        const double gy = -wk * (inv[3] * x + inv[1] * y + inv[4] * z);
-        const double gz = -wk * (inv[5] * x + inv[4] * y + inv[2] * z);
-        D.shape[base + k] = make_double4_32a(N, gx, gy, gz);
+        const double ex = N * x, ey = N * y, ez = N * z;
+        D.shape[base + k] = make_double4_32a(N, ex, ey, ez);
         const int id = D.ids[base + k];
         const int64_t pos = (int64_t)D.noff[id] + D.rank[base + k];
         double sx = 0.0, sy = 0.0, sz = 0.0;
@@ -905,11 +891,11 @@ __global__ void __launch_bounds__(kLmeWarps * kWarp) k_lme(const Dev D)
             }
         }
         if (MIXED) {
-            const float fgx = (float)gx, fgy = (float)gy, fgz = (float)gz;
+            const float fex = (float)ex, fey = (float)ey, fez = (float)ez;
             const float c0 = (float)(mp * N);
-            float c1 = fmaf(fsxz, fgz, fmaf(fsxy, fgy, fsxx * fgx));
-            float c2 = fmaf(fsyz, fgz, fmaf(fsyy, fgy, fsxy * fgx));
-            float c3 = fmaf(fszz, fgz, fmaf(fsyz, fgy, fsxz * fgx));
+            float c1 = fmaf(Qf[2], fez, fmaf(Qf[1], fey, Qf[0] * fex));
+            float c2 = fmaf(Qf[5], fez, fmaf(Qf[4], fey, Qf[3] * fex));
+            float c3 = fmaf(Qf[8], fez, fmaf(Qf[7], fey, Qf[6] * fex));
             if (STAB) {
                 c1 += (float)sx;
                 c2 += (float)sy;
@@ -920,9 +906,9 @@ __global__ void __launch_bounds__(kLmeWarps * kWarp) k_lme(const Dev D)
             ef = max(ef, max(fexp32(c1), max(fexp32(c2), fexp32(c3))));
         } else {
             const double cm = mp * N;
-            double fx = sxx * gx + sxy * gy + sxz * gz;
-            double fy = sxy * gx + syy * gy + syz * gz;
-            double fz = sxz * gx + syz * gy + szz * gz;
+            double fx = Q[0] * ex + Q[1] * ey + Q[2] * ez;
+            double fy = Q[3] * ex + Q[4] * ey + Q[5] * ez;
+            double fz = Q[6] * ex + Q[7] * ey + Q[8] * ez;
             if (STAB) {
                 fx += sx;
                 fy += sy;
@@ -964,9 +950,11 @@ cudaError_t launch_lme(const Dev &D, cudaStream_t s, long long *launches)
 
 // (N, grad N) of every slot of a padded row set, for state export: already stored in shape[]
 // ======================================================================== k_kinematics
-// warp per MP: the 12 sums x_p,i = sum N x_a,i and (dF - 1)_ij = sum du_a,i dN_a/dx_j over the old
-// support; lanes 2j write sum j. The products with F, det(dF) and the volume update follow in
-// the thread-per-MP return-map kernel.
+// warp per MP: the 12 sums x_p,i = sum N x_a,i and G_ij = sum du_a,i e_a,j (e_a = N_a d_a, the
+// stored pair row) over the old support; lanes 2j write sum j. Eq. 11 is then
+// dF = 1 + sum du_a (x) grad N_a = 1 - G K with K = J^-1 of the old support's LME solve, formed
+// once per MP in the thread-per-MP return-map kernel with the products with F, det(dF) and the
+// volume update.
 template <bool MIXED>
 __global__ void __launch_bounds__(128) k_kinematics(const Dev D)
 {
@@ -1000,8 +988,7 @@ __global__ void __launch_bounds__(128) k_kinematics(const Dev D)
             ((double *)&D.xp[p])[j] = t;
             if (!isfinite(t)) raise_error(D.err, OTM_ERR_NONFINITE, D.mgid[p]);
         } else {
-            const int c = j - 3;   // row-major (i, j) of dF
-            D.dF[9 * p + c] = (c == 0 || c == 4 || c == 8) ? 1.0 + t : t;
+            D.dF[9 * p + (j - 3)] = t;   // row-major G = sum du (x) e; k_return_map forms dF
         }
     }
 }
@@ -1024,7 +1011,19 @@ __global__ void __launch_bounds__(128) k_return_map(const Dev D)
     if (p >= D.nm) return;
     if (has_error(D.err)) return;
     RmIn in;
-    for (int i = 0; i < 9; i++) in.dF[i] = D.dF[9 * p + i];
+    {   // Eq. 11: dF = 1 + sum du_a (x) grad N_a = 1 - G K (G from the kinematics gather, K = J^-1
+        // of the LME solve the gather's shape functions came from)
+        double G[9];
+        for (int i = 0; i < 9; i++) G[i] = D.dF[9 * p + i];
+        const double *k = D.Kinv + 6 * p;
+        const double K[9] = {k[0], k[3], k[5], k[3], k[1], k[4], k[5], k[4], k[2]};
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) {
+                const double gk = G[3 * i] * K[j] + G[3 * i + 1] * K[3 + j] + G[3 * i + 2] * K[6 + j];
+                in.dF[3 * i + j] = (i == j ? 1.0 : 0.0) - gk;
+            }
+        for (int i = 0; i < 9; i++) D.dF[9 * p + i] = in.dF[i];
+    }
     const double *d = in.dF;
     // Eq. 10-12: F_{n+1} = dF F_n, v_{n+1} = det(dF) v_n
     const double det = d[0] * (d[4] * d[8] - d[5] * d[7]) - d[1] * (d[3] * d[8] - d[5] * d[6]) +
