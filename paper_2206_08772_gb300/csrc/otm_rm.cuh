@@ -171,7 +171,9 @@ __device__ inline int return_map_point(const otm_material &M, double dt, const R
         const double na = (sn > 0.0) ? s[a] / sn : 0.0;
         e[a] -= dgamma * na;
         tau[a] = K * tr + 2.0 * mu * (e[a] - tr / 3.0);
-        eb2[a] = exp(2.0 * e[a]);
+        // b^e = Q diag(exp(2 e)) Q^T; without plastic flow e = ln(lambda) / 2 of the trial, so the
+        // eigenvalues are the trial's own
+        eb2[a] = (dep > 0.0) ? exp(2.0 * e[a]) : A[a][a];
     }
     const double iJ = 1.0 / in.J;
     const int I[6] = {0, 1, 2, 0, 1, 0}, Jx[6] = {0, 1, 2, 1, 2, 2};
