@@ -606,7 +606,8 @@ def main():
         torch.cuda.empty_cache()
         mv = world * prob.n_mps * args.steps / (infom["ms"] / 1e3)
         mixed = {"value": mv, "unit": UNIT, "ms_per_step": infom["ms"] / args.steps,
-                 "speedup_vs_fp64": mv / value, "dtype": "f32 scatter/node update, f64 elsewhere",
+                 "speedup_vs_fp64": mv / value,
+                 "dtype": "f32 scatter/node update, double-float LME Hessian sums, f64 elsewhere",
                  "phases_ms": phases_m}
     adjoint = None
     if not args.no_adjoint and rank == 0:

@@ -55,7 +55,8 @@ extern "C" {
 #define OTM_ERR_CAPACITY (-8)         /* support / influence / cell capacity exceeded */
 
 #define OTM_PRECISION_FP64 0          /* every step in FP64 */
-#define OTM_PRECISION_MIXED 1         /* FP32 force scatter and node update, FP64 elsewhere */
+#define OTM_PRECISION_MIXED 1         /* FP32 force scatter and node update, the LME Newton's Hessian
+                                       * sums in double-float (FP32 pairs, ~2^-47); FP64 elsewhere */
 
 #define OTM_FLAG_FIXED 1              /* node flag: displacement increment held at zero */
 

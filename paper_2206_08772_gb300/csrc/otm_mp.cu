@@ -462,41 +462,151 @@ __device__ __forceinline__ void newton_set_trial(MpNewton &m)
 // One evaluation of the block path (Eq. 14 sums at the pending trial of MP state m): weights
 // into W.w, the sums into m.E (written by one lane per value), m.E[10] = the shift used. If Z
 // over- or underflows, again with the shift at the largest exponent. Warp-uniform.
-template <bool SHIFTED>
+// ---- double-float arithmetic for the Hessian sums (FP32 pairs hi + lo, about 2^-47 relative)
+// An FP64 value split into two FP32 values with integer operations on its bits (GB300 charges a
+// conversion instruction an FP64-pipe slot): hi = the leading 24 significant bits, lo = the next
+// 24 of the remaining 29 (truncated), so v = hi + lo to 2^-47 relative. Values outside the normal
+// FP32 range give hi = lo = 0 (the Hessian sums only see weights in [1e-30, 1e30], checked by the
+// caller, and differences of about h).
+__device__ __forceinline__ void df_split(double v, float &hi, float &lo)
+{
+    const int vh = __double2hiint(v);
+    const unsigned vl = (unsigned)__double2loint(v);
+    const int e = ((vh >> 20) & 0x7ff) - 1023;
+    const unsigned sgn = (unsigned)vh & 0x80000000u;
+    const bool ok = e > -126 && e < 128;
+    hi = ok ? __uint_as_float(sgn | ((unsigned)(e + 127) << 23) | ((unsigned)(vh & 0xfffff) << 3) | (vl >> 29))
+            : 0.f;
+    const unsigned r = vl & 0x1fffffffu;   // significand bits 28..0 below hi, weight 2^(e - 52)
+    const int lz = __clz(r);               // >= 3 when r != 0
+    const int el = e - 52 + (31 - lz);     // exponent of r's leading bit
+    lo = (ok && r != 0 && el > -126) ? __uint_as_float(sgn | ((unsigned)(el + 127) << 23) | (((r << lz) << 1) >> 9))
+                                     : 0.f;
+}
+
+// exact widening of an FP32 value to FP64 with integer operations (zero and normal values)
+__device__ __forceinline__ double df_widen(float f)
+{
+    const unsigned b = __float_as_uint(f);
+    const unsigned ef = (b >> 23) & 0xff;
+    if (ef == 0) return 0.0;
+    return __hiloint2double((int)((b & 0x80000000u) | ((ef - 127 + 1023) << 20) | ((b & 0x7fffffu) >> 3)),
+                            (int)(b << 29));
+}
+
+// (p, e) ~ (ah + al)(bh + bl): the product and its error, the al bl term dropped
+__device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float &p, float &e)
+{
+    p = ah * bh;
+    e = fmaf(ah, bh, -p);
+    e = fmaf(ah, bl, e);
+    e = fmaf(al, bh, e);
+}
+
+// (sh, sl) += (q, f) with an error-free sum of the leading parts
+__device__ __forceinline__ void df_add(float &sh, float &sl, float q, float f)
+{
+    const float s = sh + q;
+    const float t = s - sh;
+    const float err = (sh - (s - t)) + (q - t);
+    sl = sl + (err + f);
+    sh = s;
+}
+
+// One evaluation's sums over the pairs of lane `lane`: Z, r = sum w d and A = sum w d d^T.
+// FP64 path (DFH false): all in FP64. Mixed path (DFH true): Z and r in FP64 (r is a cancelling
+// sum that decides convergence at 1e-14 h), the Hessian sums A in double-float: they only set
+// the Newton step and J^-1, for which their relative accuracy of about 1e-14 is ample, and they
+// then leave the FP64 pipe, the kernel's bound, to the weights; the per-lane double-float sums are
+// widened to FP64 before the warp reduction.
+template <bool SHIFTED, bool DFH>
 __device__ __forceinline__ void lme_acc10(const WarpSmem &W, int n, double s0, double s1, double s2, double qs,
                                           int lane, const double *T, double (&v)[10])
 {
 #pragma unroll
     for (int i = 0; i < 10; i++) v[i] = 0.0;
+    if (!DFH) {
+        for (int k = lane; k < n; k += kWarp) {
+            const double x = W.dx[k], y = W.dy[k], z = W.dz[k];
+            const double qk = SHIFTED ? W.q[k] + qs : W.q[k];
+            const double wk = exp_scaled(fma(s2, z, fma(s1, y, fma(s0, x, qk))), T);
+            W.w[k] = wk;
+            const double wx = wk * x, wy = wk * y, wz = wk * z;
+            v[0] += wk;
+            v[1] += wx; v[2] += wy; v[3] += wz;
+            v[4] = fma(wx, x, v[4]); v[5] = fma(wy, y, v[5]); v[6] = fma(wz, z, v[6]);
+            v[7] = fma(wx, y, v[7]); v[8] = fma(wy, z, v[8]); v[9] = fma(wx, z, v[9]);
+        }
+        return;
+    }
+    float ah[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, al[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (int k = lane; k < n; k += kWarp) {
         const double x = W.dx[k], y = W.dy[k], z = W.dz[k];
         const double qk = SHIFTED ? W.q[k] + qs : W.q[k];
         const double wk = exp_scaled(fma(s2, z, fma(s1, y, fma(s0, x, qk))), T);
         W.w[k] = wk;
-        const double wx = wk * x, wy = wk * y, wz = wk * z;
         v[0] += wk;
-        v[1] += wx; v[2] += wy; v[3] += wz;
+        v[1] = fma(wk, x, v[1]); v[2] = fma(wk, y, v[2]); v[3] = fma(wk, z, v[3]);
+        float wh, wl, xh, xl, yh, yl, zh, zl;
+        df_split(wk, wh, wl);
+        df_split(x, xh, xl);
+        df_split(y, yh, yl);
+        df_split(z, zh, zl);
+        float pxh, pxl, pyh, pyl, pzh, pzl, q, f;
+        df_mul(wh, wl, xh, xl, pxh, pxl);
+        df_mul(wh, wl, yh, yl, pyh, pyl);
+        df_mul(wh, wl, zh, zl, pzh, pzl);
+        df_mul(pxh, pxl, xh, xl, q, f); df_add(ah[0], al[0], q, f);
+        df_mul(pyh, pyl, yh, yl, q, f); df_add(ah[1], al[1], q, f);
+        df_mul(pzh, pzl, zh, zl, q, f); df_add(ah[2], al[2], q, f);
+        df_mul(pxh, pxl, yh, yl, q, f); df_add(ah[3], al[3], q, f);
+        df_mul(pyh, pyl, zh, zl, q, f); df_add(ah[4], al[4], q, f);
+        df_mul(pxh, pxl, zh, zl, q, f); df_add(ah[5], al[5], q, f);
+    }
+#pragma unroll
+    for (int i = 0; i < 6; i++) v[4 + i] = df_widen(ah[i]) + df_widen(al[i]);
+}
+
+// The FP64 Hessian sums of one evaluation from its stored weights (the fallback for weights
+// outside the double-float range; see lme_eval_block)
+__device__ __forceinline__ void lme_hessian64(const WarpSmem &W, int n, int lane, double (&v)[10])
+{
+    for (int k = lane; k < n; k += kWarp) {
+        const double x = W.dx[k], y = W.dy[k], z = W.dz[k];
+        const double wk = W.w[k];
+        const double wx = wk * x, wy = wk * y, wz = wk * z;
         v[4] = fma(wx, x, v[4]); v[5] = fma(wy, y, v[5]); v[6] = fma(wz, z, v[6]);
         v[7] = fma(wx, y, v[7]); v[8] = fma(wy, z, v[8]); v[9] = fma(wx, z, v[9]);
     }
 }
 
+template <bool DFH>
 __device__ void lme_eval_block(const WarpSmem &W, int n, MpNewton &m, int lane, const double *T)
 {
     const double s0 = m.ts[0], s1 = m.ts[1], s2 = m.ts[2];
     double qs = m.qs, sh = m.sh;
     double v[10];
-    if (qs == 0.0) lme_acc10<false>(W, n, s0, s1, s2, qs, lane, T, v);
-    else lme_acc10<true>(W, n, s0, s1, s2, qs, lane, T, v);
+    if (qs == 0.0) lme_acc10<false, DFH>(W, n, s0, s1, s2, qs, lane, T, v);
+    else lme_acc10<true, DFH>(W, n, s0, s1, s2, qs, lane, T, v);
     double t = warp_reduce_scatter10(v, lane);
-    const double Z = __shfl_sync(0xffffffffu, t, 0);
+    double Z = __shfl_sync(0xffffffffu, t, 0);
     if (!(Z > 1e-200) || !(Z < 1e200)) {
         double mx = -INFINITY;
         for (int k = lane; k < n; k += kWarp) mx = fmax(mx, W.q[k] + (s0 * W.dx[k] + s1 * W.dy[k] + s2 * W.dz[k]));
         sh = warp_max(mx) * (1.0 / kExpScale) + m.shift0;
         qs = (m.shift0 - sh) * kExpScale;
-        lme_acc10<true>(W, n, s0, s1, s2, qs, lane, T, v);
+        lme_acc10<true, DFH>(W, n, s0, s1, s2, qs, lane, T, v);
         t = warp_reduce_scatter10(v, lane);
+        Z = __shfl_sync(0xffffffffu, t, 0);
+    }
+    if (DFH && !(Z >= 1e-30 && Z <= 1e30)) {
+        // weights this far from 1 may leave the FP32 range of the double-float sums: the Hessian
+        // sums again in FP64 from the stored weights (Z and r are kept)
+#pragma unroll
+        for (int i = 4; i < 10; i++) v[i] = 0.0;
+        lme_hessian64(W, n, lane, v);
+        const double t2 = warp_reduce_scatter10(v, lane);
+        if (rs10_value(lane) >= 4) t = t2;
     }
     if (rs10_writer(lane)) m.E[rs10_value(lane)] = t;
     if (lane == 0) m.E[10] = sh;
@@ -802,7 +912,7 @@ __global__ void __launch_bounds__(kLmeWarps * kWarp) k_lme(const Dev D)
     for (;;) {
         if (M.state == kNewtonEval) {
             __syncwarp();
-            lme_eval_block(W, cnt, M, lane, T);
+            lme_eval_block<MIXED>(W, cnt, M, lane, T);
         }
         __syncthreads();
         bool pending = false;
