@@ -424,19 +424,24 @@ def run_sweep(args, torch):
         A, B = 90e6 * float(rng.uniform(0.9, 1.1)), 292e6 * float(rng.uniform(0.9, 1.1))
         prob = scenarios.taylor_rod(h=float(h), material=scenarios.copper_jc(A=A, B=B), v0=v0, seed=i,
                                     name=f"sweep_{i}")
+        # 1000 steps of a coarse rod cover up to 4x the physical time of the finest (the step is
+        # proportional to h): its mushroomed edge can carry points out of their supports' hulls,
+        # which node insertion (otm_step) repairs
+        prob.max_insert = max(1000, prob.n_nodes // 20)
         res = {}
         for prec in ("fp64", "mixed"):
             sim, info = time_gpu(prob, prec, args.sweep_steps, 3, torch, None)
             L_, R_ = objectives_and_seeds(sim.get("node_x"), sim.get("node_mass"), prob.h)[0]
-            res[prec] = (info["ms"], L_, R_)
+            res[prec] = (info["ms"], L_, R_, sim.counts()["n_nodes"] - prob.n_nodes)
             sim.close()
             del sim
             torch.cuda.empty_cache()
-        (t64, L64, R64), (t32, L32, R32) = res["fp64"], res["mixed"]
+        (t64, L64, R64, ins64), (t32, L32, R32, ins32) = res["fp64"], res["mixed"]
         rows.append({"h_mm": float(h) * 1e3, "n_mps": prob.n_mps, "v0": v0, "A": A, "B": B,
                      "fp64_ms_per_step": t64 / args.sweep_steps, "mixed_ms_per_step": t32 / args.sweep_steps,
                      "speedup": t64 / t32, "rel_err_length": abs(L32 - L64) / L64,
-                     "rel_err_radius": abs(R32 - R64) / R64})
+                     "rel_err_radius": abs(R32 - R64) / R64, "inserted_nodes_fp64": ins64,
+                     "inserted_nodes_mixed": ins32})
         print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
     tot64 = sum(r["fp64_ms_per_step"] * r["n_mps"] for r in rows)
     print(json.dumps({"sweep": "mixed vs fp64, 16 JC rods", "steps": args.sweep_steps + 3, "rods": rows,

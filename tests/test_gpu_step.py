@@ -287,6 +287,28 @@ def test_snapshot_loads_across_precisions(orc, OTM):
     assert rel(m.get("sigma"), o.get("sigma")) <= 1e-3
 
 
+def test_mixed_lme_hessian_sums_against_fp64(OTM):
+    """The mixed path accumulates the LME Newton's Hessian sums in double-float (FP32 pairs);
+    its weights, Z and residual stay FP64. Loaded from the same FP64-path snapshot, the mixed
+    handle regenerates the same supports, bit-identical N (w / Z, FP64) and grad N = -J^-1 N d
+    within 1e-11 of the FP64 path's (J^-1 from the double-float sums)."""
+    p = scenarios.taylor_rod(h=0.8e-3, R=3.2e-3, L=9.6e-3, material=scenarios.copper_jc())
+    a = OTM(p, precision="fp64")
+    assert a.step(12) == 0
+    snap = a.snapshot()
+    m = OTM(p, precision="mixed")
+    m.restore(snap)
+    oa, ia = a.supports()
+    om, im = m.supports()
+    assert np.array_equal(oa, om) and np.array_equal(ia, im)
+    Na, dNa = a.shape_functions()
+    Nm, dNm = m.shape_functions()
+    assert np.array_equal(Na, Nm)
+    e = rel(dNm, dNa)
+    print("grad N, double-float Hessian sums vs FP64:", e)
+    assert 0.0 < e <= 1e-11
+
+
 def test_pitched_state_transfer_round_trip(OTM):
     """otm_state / otm_set_state of the fields stored with padding (node x, du, mass, force, MP x)
     move exact bytes in both directions."""
