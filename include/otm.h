@@ -295,6 +295,7 @@ int otm_adjoint_result(otm_handle *h, void *adj_ws, const double *du0_ds, double
 
 /* ---------------------------------------------------------------------------------------
  * Stand-alone kernels (device pointers, caller-owned; enqueued on `stream`, not synchronised)
+ * With a point count of 0 the per-point arrays may be NULL and nothing is launched.
  * ------------------------------------------------------------------------------------- */
 
 /* Bytes of scratch needed by otm_support_search for n_nodes nodes. */

@@ -144,6 +144,56 @@ def test_return_map_vs_oracle(orc, otm, model):
     assert (eb_g > ebar).any()     # the sample crosses the yield surface
 
 
+def test_empty_point_sets(otm):
+    """Zero points: the stand-alone search, LME and return map launch nothing and report OK."""
+    nodes = dev(np.random.default_rng(0).uniform(0, 1, (50, 3)))
+    empty = torch.empty((0, 3), dtype=torch.float64, device="cuda")
+    ids, counts, grid, status = otm.support_search(nodes, empty, 0.04, 0.2, max_support=64)
+    torch.cuda.synchronize()
+    assert ids.shape == (0, 64) and counts.numel() == 0 and int(status.item()) == 0
+    shape, lam, iters, st = otm.lme(nodes, empty, ids, counts, beta=20.0, tol_abs=1e-14)
+    torch.cuda.synchronize()
+    assert shape.shape == (0, 64, 4) and int(st.item()) == 0
+    z = torch.empty((0, 9), dtype=torch.float64, device="cuda")
+    sig, rate, failed, st = otm.return_map(scenarios.copper_jc(), 1e-8, z, z.clone(),
+                                           torch.empty((0, 6), dtype=torch.float64, device="cuda"),
+                                           torch.empty(0, dtype=torch.float64, device="cuda"),
+                                           torch.empty(0, dtype=torch.float64, device="cuda"))
+    torch.cuda.synchronize()
+    assert sig.shape == (0, 6) and int(st.item()) == 0
+
+
+def test_lme_degenerate_supports(orc, otm):
+    """Degenerate cases of Eq. 14. One node, or a point on the far side of a plane of nodes: no
+    finite lambda puts the point inside the hull, so the solve fails (LME_NOCONV) on both sides.
+    Four affinely independent nodes: N are the barycentric coordinates and grad N the constant
+    tetrahedron gradients for any beta (the consistency conditions fix them), on the GPU to 1e-12."""
+    beta, tol = 0.8 / 0.01 ** 2, 1e-14 * 0.01
+    tet = np.array([[0.0, 0.0, 0.0], [0.01, 0.0, 0.0], [0.0, 0.01, 0.0], [0.0, 0.0, 0.01]])
+    cases = {"one_node": (tet[:1], np.array([0.002, 0.001, 0.0])),
+             "outside_plane": (tet[1:], np.array([0.0, 0.0, -0.001])),
+             "tet": (tet, np.array([0.002, 0.003, 0.001]))}
+    for name, (nx, xp) in cases.items():
+        n = nx.shape[0]
+        ids = torch.full((1, 32), -1, dtype=torch.int32, device="cuda")
+        ids[0, :n] = torch.arange(n, dtype=torch.int32, device="cuda")
+        counts = torch.tensor([n], dtype=torch.int32, device="cuda")
+        shape, lam, iters, st = otm.lme(dev(nx), dev(xp[None, :]), ids, counts, beta=beta, tol_abs=tol)
+        torch.cuda.synchronize()
+        so, No, dNo, _, _ = orc.lme(xp[None, :] - nx, beta, tol)
+        if name == "tet":
+            assert int(st.item()) == 0 and so == 0
+            A = np.vstack([np.ones(4), nx.T])                      # barycentric: A N = (1, x_p)
+            N = np.linalg.solve(A, np.concatenate([[1.0], xp]))
+            G = np.linalg.inv(A)[:, 1:]                            # dN/dx_p, constant
+            sh = shape.cpu().numpy()[0, :4]
+            assert np.abs(sh[:, 0] - N).max() <= 1e-12
+            assert np.abs(sh[:, 1:] - G).max() <= 1e-12 * np.abs(G).max()
+            assert rel(sh[:, 0], No) <= 1e-12 and rel(sh[:, 1:], dNo) <= 1e-12
+        else:
+            assert int(st.item()) == -4 and so == -4, name
+
+
 def test_internal_exp_against_cuda_exp():
     """The LME weights use the library's table-driven FP64 exp (after Tang 1989) on a scaled
     argument y = f 1024/ln2; it must agree with CUDA's exp of the same f to a few ulps over the
