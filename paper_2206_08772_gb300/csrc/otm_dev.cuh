@@ -206,26 +206,27 @@ __device__ __forceinline__ double warp_reduce_scatter16(const double (&v)[16], i
 // warp total of value rs12_value(L) = 6 [L & 16] + 3 [L & 8] + (1 if L & 2, else 2 if L & 4,
 // else 0); every value is held by lane pairs (2k, 2k+1), and rs12_writer(L) picks one lane per
 // value.
-__device__ __forceinline__ double warp_reduce_scatter12(const double (&v)[12], int lane)
+template <typename T>
+__device__ __forceinline__ T warp_reduce_scatter12(const T (&v)[12], int lane)
 {
-    double a[6], b[3];
+    T a[6], b[3];
 #pragma unroll
     for (int i = 0; i < 6; i++) {
         const bool up = lane & 16;
-        const double mine = up ? v[6 + i] : v[i], other = up ? v[i] : v[6 + i];
+        const T mine = up ? v[6 + i] : v[i], other = up ? v[i] : v[6 + i];
         a[i] = mine + __shfl_xor_sync(0xffffffffu, other, 16);
     }
 #pragma unroll
     for (int i = 0; i < 3; i++) {
         const bool up = lane & 8;
-        const double mine = up ? a[3 + i] : a[i], other = up ? a[i] : a[3 + i];
+        const T mine = up ? a[3 + i] : a[i], other = up ? a[i] : a[3 + i];
         b[i] = mine + __shfl_xor_sync(0xffffffffu, other, 8);
     }
     const bool up4 = lane & 4;
-    const double c0 = (up4 ? b[2] : b[0]) + __shfl_xor_sync(0xffffffffu, up4 ? b[0] : b[2], 4);
-    const double c1 = b[1] + __shfl_xor_sync(0xffffffffu, b[1], 4);
+    const T c0 = (up4 ? b[2] : b[0]) + __shfl_xor_sync(0xffffffffu, up4 ? b[0] : b[2], 4);
+    const T c1 = b[1] + __shfl_xor_sync(0xffffffffu, b[1], 4);
     const bool up2 = lane & 2;
-    const double d = (up2 ? c1 : c0) + __shfl_xor_sync(0xffffffffu, up2 ? c0 : c1, 2);
+    const T d = (up2 ? c1 : c0) + __shfl_xor_sync(0xffffffffu, up2 ? c0 : c1, 2);
     return d + __shfl_xor_sync(0xffffffffu, d, 1);
 }
 

@@ -748,11 +748,98 @@ __global__ void __launch_bounds__(kSearchWarps * kWarp) k_search(const Dev D)
     if (lane == 0) D.cnt[p] = cnt;
 }
 
+// ======================================================================== kinematics gathers
+// FP64 -> FP32, rounded to nearest (ties away from zero), with integer operations on the bits: a
+// conversion instruction takes an FP64-pipe slot on this GPU, integer operations do not. Values
+// below the normal FP32 range give a signed zero; |v| < 2^127 is assumed (shape-function values,
+// their products with separations, and force contributions).
+__device__ __forceinline__ float f32_round_bits(double v)
+{
+    const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
+    const int e = (int)((hi >> 20) & 0x7ffu) - 1023;
+    const unsigned sgn = hi & 0x80000000u;
+    const unsigned mag = ((unsigned)(e + 127) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+    return __uint_as_float(e < -126 ? sgn : (sgn | (mag + ((lo >> 28) & 1u))));
+}
+
+// The 12 sums of the kinematics over MP p's old support (n pairs at row base), reduce-scattered
+// (value rs12_value(lane) at each lane): 0-2 the x_p sums, 3-11 G = sum du_a (x) e_a row-major.
+//  FP64 path: x_p = sum N_a x_a of the updated node positions (Eq. 9), G from the FP64 increments.
+//  Mixed path, in FP32 from the FP32 increments and the pair rows rounded to FP32: with c = the
+//  increment of the support's first node, values 0-2 are sum N_a (du_a - c) and G =
+//  sum (du_a - c) (x) e_a. Then x_p,n+1 = x_p,n + c + sum N_a (du_a - c), which is Eq. 9 by the
+//  partition of unity and the linear reproducibility of the LME functions (sum N_a x_a,n = x_p,n
+//  to the Newton tolerance), and G differs from the FP64 sum by c (x) sum e_a = c (x) r / Z, below
+//  |c| 1e-14 h. Subtracting c leaves only the deforming part of the increments in the FP32 sums
+//  (no cancellation of the rigid translation), so their error is FP32 rounding of the deformation.
+template <bool MIXED>
+struct KinSum;
+
+template <>
+struct KinSum<false> {
+    double t;
+    __device__ __forceinline__ void gather(const Dev &D, int64_t base, int n, int lane)
+    {
+        double v[12];
+#pragma unroll
+        for (int i = 0; i < 12; i++) v[i] = 0.0;
+        for (int k = lane; k < n; k += kWarp) {
+            const int id = D.ids[base + k];
+            const double4_32a sh = D.shape[base + k];
+            const double4_32a xa = D.x[id];
+            const double4_32a u = D.du[id];
+            v[0] = fma(sh.x, xa.x, v[0]); v[1] = fma(sh.x, xa.y, v[1]); v[2] = fma(sh.x, xa.z, v[2]);
+            v[3] = fma(u.x, sh.y, v[3]); v[4] = fma(u.x, sh.z, v[4]); v[5] = fma(u.x, sh.w, v[5]);
+            v[6] = fma(u.y, sh.y, v[6]); v[7] = fma(u.y, sh.z, v[7]); v[8] = fma(u.y, sh.w, v[8]);
+            v[9] = fma(u.z, sh.y, v[9]); v[10] = fma(u.z, sh.z, v[10]); v[11] = fma(u.z, sh.w, v[11]);
+        }
+        t = warp_reduce_scatter12(v, lane);
+    }
+    __device__ __forceinline__ double g() const { return t; }
+    // x_p,n+1 component i, on the lane that holds value i (lanes 0, 2, 4)
+    __device__ __forceinline__ double xp(double, int) const { return t; }
+};
+
+template <>
+struct KinSum<true> {
+    float t;
+    float c[3];
+    __device__ __forceinline__ void gather(const Dev &D, int64_t base, int n, int lane)
+    {
+        float v[12];
+#pragma unroll
+        for (int i = 0; i < 12; i++) v[i] = 0.f;
+        float4 c4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (n > 0) c4 = D.du32[D.ids[base]];
+        c[0] = c4.x; c[1] = c4.y; c[2] = c4.z;
+        for (int k = lane; k < n; k += kWarp) {
+            const int id = D.ids[base + k];
+            const double4_32a sh = D.shape[base + k];
+            const float4 u = D.du32[id];
+            const float N = f32_round_bits(sh.x), ex = f32_round_bits(sh.y), ey = f32_round_bits(sh.z),
+                        ez = f32_round_bits(sh.w);
+            const float a0 = u.x - c4.x, a1 = u.y - c4.y, a2 = u.z - c4.z;
+            v[0] = fmaf(N, a0, v[0]); v[1] = fmaf(N, a1, v[1]); v[2] = fmaf(N, a2, v[2]);
+            v[3] = fmaf(a0, ex, v[3]); v[4] = fmaf(a0, ey, v[4]); v[5] = fmaf(a0, ez, v[5]);
+            v[6] = fmaf(a1, ex, v[6]); v[7] = fmaf(a1, ey, v[7]); v[8] = fmaf(a1, ez, v[8]);
+            v[9] = fmaf(a2, ex, v[9]); v[10] = fmaf(a2, ey, v[10]); v[11] = fmaf(a2, ez, v[11]);
+        }
+        t = warp_reduce_scatter12(v, lane);
+    }
+    __device__ __forceinline__ double g() const { return (double)t; }
+    __device__ __forceinline__ double xp(double old, int i) const
+    {
+        const float ci = i == 0 ? c[0] : (i == 1 ? c[1] : c[2]);
+        return old + ((double)ci + (double)t);
+    }
+};
+
 // ======================================================================== k_kin_search
 // Kinematics (Eq. 9, 11) and the support search at the new position (Algorithm 3) in one warp
 // per MP: the gather over the old support gives x_p and dF, then the candidate scan builds the
 // new support in the same row. Used when no erosion can remove MPs between the two; the
 // return map (which only needs dF) follows.
+template <bool MIXED>
 __global__ void __launch_bounds__(kSearchWarps * kWarp) k_kin_search(const Dev D)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -763,25 +850,15 @@ __global__ void __launch_bounds__(kSearchWarps * kWarp) k_kin_search(const Dev D
     const int S = D.S;
     const int n = D.cnt[p];
     const int64_t base = p * (int64_t)S;
-    double v[12];
-#pragma unroll
-    for (int i = 0; i < 12; i++) v[i] = 0.0;
-    for (int k = lane; k < n; k += kWarp) {
-        const int id = D.ids[base + k];
-        const double4_32a sh = D.shape[base + k];
-        const double4_32a xa = D.x[id];
-        const double4_32a u = D.du[id];
-        v[0] = fma(sh.x, xa.x, v[0]); v[1] = fma(sh.x, xa.y, v[1]); v[2] = fma(sh.x, xa.z, v[2]);
-        v[3] = fma(u.x, sh.y, v[3]); v[4] = fma(u.x, sh.z, v[4]); v[5] = fma(u.x, sh.w, v[5]);
-        v[6] = fma(u.y, sh.y, v[6]); v[7] = fma(u.y, sh.z, v[7]); v[8] = fma(u.y, sh.w, v[8]);
-        v[9] = fma(u.z, sh.y, v[9]); v[10] = fma(u.z, sh.z, v[10]); v[11] = fma(u.z, sh.w, v[11]);
-    }
-    const double t = warp_reduce_scatter12(v, lane);
+    KinSum<MIXED> ks;
+    ks.gather(D, base, n, lane);
     const int j = rs12_value(lane);
-    if (rs12_writer(lane) && j >= 3) D.dF[9 * p + (j - 3)] = t;   // G = sum du (x) e; k_return_map forms dF
+    if (rs12_writer(lane) && j >= 3) D.dF[9 * p + (j - 3)] = ks.g();   // G = sum du (x) e; k_return_map forms dF
     // values 0, 1, 2 (x_p) sit at lanes 0, 2, 4
-    const double px = __shfl_sync(0xffffffffu, t, 0), py = __shfl_sync(0xffffffffu, t, 2),
-                 pz = __shfl_sync(0xffffffffu, t, 4);
+    double xi = 0.0;
+    if (lane < 6 && (lane & 1) == 0) xi = ks.xp(((const double *)&D.xp[p])[lane >> 1], lane >> 1);
+    const double px = __shfl_sync(0xffffffffu, xi, 0), py = __shfl_sync(0xffffffffu, xi, 2),
+                 pz = __shfl_sync(0xffffffffu, xi, 4);
     if (lane == 0) {
         D.xp_prev[p] = D.xp[p];
         D.xp[p] = make_double4_32a(px, py, pz, 0.0);
@@ -814,7 +891,10 @@ cudaError_t launch_kin_search(const Dev &D, cudaStream_t s, long long *launches)
     const size_t smem = (size_t)kSearchWarps * next_pow2(D.S) * sizeof(int32_t);
     const unsigned blocks = (unsigned)((D.nm + kSearchWarps - 1) / kSearchWarps);
     if (blocks == 0) return cudaSuccess;
-    k_kin_search<<<blocks, kSearchWarps * kWarp, smem, s>>>(D);
+    if (D.precision == OTM_PRECISION_MIXED)
+        k_kin_search<true><<<blocks, kSearchWarps * kWarp, smem, s>>>(D);
+    else
+        k_kin_search<false><<<blocks, kSearchWarps * kWarp, smem, s>>>(D);
     if (launches) *launches += 1;
     return cudaGetLastError();
 }
@@ -970,6 +1050,7 @@ __global__ void __launch_bounds__(kLmeWarps * kWarp) k_lme(const Dev D)
     float Qf[9];
 #pragma unroll
     for (int i = 0; i < 9; i++) Qf[i] = MIXED ? (float)Q[i] : 0.f;
+    const float mpf = MIXED ? (float)mp : 0.f;
     // stabilisation (Eq. 7-8): -eps N_a e_a / |x_a,n-1 - x_p,n-1|,
     // e_a = x_a - x_p - dF (x_a,n-1 - x_p,n-1), with dF the increment that led to this state
     double xq0 = 0, xq1 = 0, xq2 = 0, F00 = 0, F01 = 0, F02 = 0, F10 = 0, F11 = 0, F12 = 0, F20 = 0, F21 = 0, F22 = 0;
@@ -1001,15 +1082,16 @@ __global__ void __launch_bounds__(kLmeWarps * kWarp) k_lme(const Dev D)
             }
         }
         if (MIXED) {
-            const float fex = (float)ex, fey = (float)ey, fez = (float)ez;
-            const float c0 = (float)(mp * N);
+            // FP32 operands by integer rounding of the FP64 row (no FP64-pipe conversions)
+            const float fex = f32_round_bits(ex), fey = f32_round_bits(ey), fez = f32_round_bits(ez);
+            const float c0 = mpf * f32_round_bits(N);
             float c1 = fmaf(Qf[2], fez, fmaf(Qf[1], fey, Qf[0] * fex));
             float c2 = fmaf(Qf[5], fez, fmaf(Qf[4], fey, Qf[3] * fex));
             float c3 = fmaf(Qf[8], fez, fmaf(Qf[7], fey, Qf[6] * fex));
             if (STAB) {
-                c1 += (float)sx;
-                c2 += (float)sy;
-                c3 += (float)sz;
+                c1 += f32_round_bits(sx);
+                c2 += f32_round_bits(sy);
+                c3 += f32_round_bits(sz);
             }
             D.contrib32[pos] = make_float4(c0, c1, c2, c3);
             em = max(em, fexp32(c0));
@@ -1074,31 +1156,18 @@ __global__ void __launch_bounds__(128) k_kinematics(const Dev D)
     if (has_error(D.err)) return;
     const int n = D.cnt[p];
     const int64_t base = p * (int64_t)D.S;
-    double v[12];
-#pragma unroll
-    for (int i = 0; i < 12; i++) v[i] = 0.0;
-    for (int k = lane; k < n; k += kWarp) {
-        const int id = D.ids[base + k];
-        const double4_32a sh = D.shape[base + k];
-        const double4_32a xa = D.x[id];
-        // the node kernel stores every increment in FP64 as well (in the mixed path it is the
-        // FP32 increment, widened), so both paths read the FP64 copy
-        const double4_32a u = D.du[id];
-        const double u0 = u.x, u1 = u.y, u2 = u.z;
-        v[0] = fma(sh.x, xa.x, v[0]); v[1] = fma(sh.x, xa.y, v[1]); v[2] = fma(sh.x, xa.z, v[2]);
-        v[3] = fma(u0, sh.y, v[3]); v[4] = fma(u0, sh.z, v[4]); v[5] = fma(u0, sh.w, v[5]);
-        v[6] = fma(u1, sh.y, v[6]); v[7] = fma(u1, sh.z, v[7]); v[8] = fma(u1, sh.w, v[8]);
-        v[9] = fma(u2, sh.y, v[9]); v[10] = fma(u2, sh.z, v[10]); v[11] = fma(u2, sh.w, v[11]);
-    }
-    const double t = warp_reduce_scatter12(v, lane);
+    KinSum<MIXED> ks;
+    ks.gather(D, base, n, lane);
     const int j = rs12_value(lane);
     if (rs12_writer(lane)) {
         if (j < 3) {
-            ((double *)&D.xp_prev[p])[j] = ((const double *)&D.xp[p])[j];
-            ((double *)&D.xp[p])[j] = t;
-            if (!isfinite(t)) raise_error(D.err, OTM_ERR_NONFINITE, D.mgid[p]);
+            const double old = ((const double *)&D.xp[p])[j];
+            const double x = ks.xp(old, j);
+            ((double *)&D.xp_prev[p])[j] = old;
+            ((double *)&D.xp[p])[j] = x;
+            if (!isfinite(x)) raise_error(D.err, OTM_ERR_NONFINITE, D.mgid[p]);
         } else {
-            D.dF[9 * p + (j - 3)] = t;   // row-major G = sum du (x) e; k_return_map forms dF
+            D.dF[9 * p + (j - 3)] = ks.g();   // row-major G = sum du (x) e; k_return_map forms dF
         }
     }
 }

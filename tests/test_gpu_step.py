@@ -309,6 +309,28 @@ def test_mixed_lme_hessian_sums_against_fp64(OTM):
     assert 0.0 < e <= 1e-11
 
 
+def test_mixed_kinematics_gather_against_fp64(OTM):
+    """The mixed path gathers the MP displacement (Eq. 9) and G = sum du (x) e (Eq. 11) in FP32
+    from the FP32 increments, relative to the increment of one support node. From the same
+    FP64-path snapshot, one step of each path: the step's MP displacement and the strain increment
+    dF - 1 agree with the FP64 path's within 1e-5 of their largest values (the FP32 rounding of the
+    increments and of the force contributions)."""
+    p = scenarios.taylor_rod(h=0.8e-3, R=3.2e-3, L=9.6e-3, material=scenarios.copper_jc())
+    a = OTM(p, precision="fp64")
+    assert a.step(12) == 0
+    snap = a.snapshot()
+    m = OTM(p, precision="mixed")
+    m.restore(snap)
+    x0 = a.get("mp_x")
+    assert a.step(1) == 0, a.error()
+    assert m.step(1) == 0, m.error()
+    I = np.eye(3).reshape(1, 9)
+    e_dx = rel(m.get("mp_x") - x0, a.get("mp_x") - x0)
+    e_g = rel(m.get("dF") - I, a.get("dF") - I)
+    print("mixed vs FP64, one step: MP displacement", e_dx, "dF - 1", e_g)
+    assert 0.0 < e_dx <= 1e-5 and 0.0 < e_g <= 1e-5
+
+
 def test_pitched_state_transfer_round_trip(OTM):
     """otm_state / otm_set_state of the fields stored with padding (node x, du, mass, force, MP x)
     move exact bytes in both directions."""
