@@ -19,6 +19,58 @@
 
 namespace otm {
 
+// ======================================================================== double-float arithmetic
+// FP32 pairs hi + lo, about 2^-47 relative (the mixed path's Hessian sums and exp polynomial)
+// An FP64 value split into two FP32 values with integer operations on its bits (GB300 charges a
+// conversion instruction an FP64-pipe slot): hi = the leading 24 significant bits, lo = the next
+// 24 of the remaining 29 (truncated), so v = hi + lo to 2^-47 relative. Values outside the normal
+// FP32 range give hi = lo = 0 (the Hessian sums only see weights in [1e-30, 1e30], checked by the
+// caller, and differences of about h).
+__device__ __forceinline__ void df_split(double v, float &hi, float &lo)
+{
+    const int vh = __double2hiint(v);
+    const unsigned vl = (unsigned)__double2loint(v);
+    const int e = ((vh >> 20) & 0x7ff) - 1023;
+    const unsigned sgn = (unsigned)vh & 0x80000000u;
+    const bool ok = e > -126 && e < 128;
+    hi = ok ? __uint_as_float(sgn | ((unsigned)(e + 127) << 23) | ((unsigned)(vh & 0xfffff) << 3) | (vl >> 29))
+            : 0.f;
+    const unsigned r = vl & 0x1fffffffu;   // significand bits 28..0 below hi, weight 2^(e - 52)
+    const int lz = __clz(r);               // >= 3 when r != 0
+    const int el = e - 52 + (31 - lz);     // exponent of r's leading bit
+    lo = (ok && r != 0 && el > -126) ? __uint_as_float(sgn | ((unsigned)(el + 127) << 23) | (((r << lz) << 1) >> 9))
+                                     : 0.f;
+}
+
+// exact widening of an FP32 value to FP64 with integer operations (zero and normal values)
+__device__ __forceinline__ double df_widen(float f)
+{
+    const unsigned b = __float_as_uint(f);
+    const unsigned ef = (b >> 23) & 0xff;
+    if (ef == 0) return 0.0;
+    return __hiloint2double((int)((b & 0x80000000u) | ((ef - 127 + 1023) << 20) | ((b & 0x7fffffu) >> 3)),
+                            (int)(b << 29));
+}
+
+// (p, e) ~ (ah + al)(bh + bl): the product and its error, the al bl term dropped
+__device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float &p, float &e)
+{
+    p = ah * bh;
+    e = fmaf(ah, bh, -p);
+    e = fmaf(ah, bl, e);
+    e = fmaf(al, bh, e);
+}
+
+// (sh, sl) += (q, f) with an error-free sum of the leading parts
+__device__ __forceinline__ void df_add(float &sh, float &sl, float q, float f)
+{
+    const float s = sh + q;
+    const float t = s - sh;
+    const float err = (sh - (s - t)) + (q - t);
+    sl = sl + (err + f);
+    sh = s;
+}
+
 // ======================================================================== FP64 exponential
 // exp(f) by a table-driven method after P. T. P. Tang ("Table-driven implementation of the
 // exponential function in IEEE floating-point arithmetic", ACM TOMS 15(2), 1989), with the
@@ -80,6 +132,18 @@ __device__ __forceinline__ void exp_table_load(double *T)
     __syncthreads();
 }
 
+// the polynomial's coefficients as double-float pairs (C3 needs FP32 only: its term is below 7e-12)
+constexpr float kExpC1h = (float)kExpC1;
+constexpr float kExpC1l = (float)((kExpC1 - (double)kExpC1h) + kExpC1lo);
+constexpr float kExpC2h = (float)kExpC2;
+constexpr float kExpC2l = (float)(kExpC2 - (double)kExpC2h);
+constexpr float kExpC3f = (float)kExpC3;
+
+// DF = false: the polynomial p(s) = exp(s ln2/1024) - 1 in FP64 (3 FP64 instructions) and v =
+// T (1 + p) in one FMA. DF = true (mixed path): p in double-float on the FP32 pipe (s split exactly
+// enough: 2^-48 of |s| <= 1/2; p to about 2^-46 of |p| <= 3.4e-4, i.e. 5e-18 absolute), then v =
+// T + T p_hi + T p_lo in two FMAs: two FP64 instructions instead of four, with the same accuracy.
+template <bool DF = false>
 __device__ __forceinline__ double exp_scaled(double y, const double *T)
 {
     // y = n + s with n = round(y) and s exact, |s| <= 1/2. For 1 <= |y| < 2^20 (every weight of the
@@ -122,9 +186,24 @@ __device__ __forceinline__ double exp_scaled(double y, const double *T)
         sr = y - (t - kExpShifter);
     }
     if (n < kExpNmin || n > kExpNmax) return (y > 0.0) ? INFINITY : 0.0;
-    const double p = sr * fma(sr, fma(sr, kExpC3, kExpC2), kExpC1);
     const double Tj = T[n & (kExpTable - 1)];
-    const double v = fma(Tj, p, Tj);
+    double v;
+    if (DF) {
+        float sh, sl;
+        df_split(sr, sh, sl);
+        float ah = kExpC2h, al = kExpC2l;
+        df_add(ah, al, kExpC3f * sh, 0.f);            // C2 + C3 s
+        float bh, bl;
+        df_mul(ah, al, sh, sl, bh, bl);               // (C2 + C3 s) s
+        float ch = kExpC1h, cl = kExpC1l;
+        df_add(ch, cl, bh, bl);                       // C1 + (C2 + C3 s) s
+        float ph, pl;
+        df_mul(ch, cl, sh, sl, ph, pl);               // p
+        v = fma(Tj, df_widen(pl), fma(Tj, df_widen(ph), Tj));
+    } else {
+        const double p = sr * fma(sr, fma(sr, kExpC3, kExpC2), kExpC1);
+        v = fma(Tj, p, Tj);
+    }
     return __hiloint2double(__double2hiint(v) + ((n >> 10) << 20), __double2loint(v));
 }
 
@@ -362,32 +441,51 @@ __device__ int warp_support_search(const SearchGrid &G, const SearchConst &C, do
     const float e = 1.001f * u * (2.f * U + 1.5f * rs);
     const float band = 1.5f * (1.25f * (e * (9.f * rs + 3.f * e) + 3.1f * u * rs * rs) + 1e-15f * rs * rs);
     const float lo = __fsub_rd(C.rs2_rd, band), hi = __fadd_ru(C.rs2_ru, band);
-    for (int kz = z0; kz <= z1; kz++) {
-        for (int ky = y0; ky <= y1; ky++) {
-            const int rowc = (kz * ny + ky) * nx;
-            const int s0 = G.cell_start[rowc + x0], s1 = G.cell_start[rowc + x1 + 1];
-            for (int b = s0; b < s1; b += kWarp) {
-                const int s = b + lane;
-                bool acc = false;
-                int id = 0;
-                if (s < s1) {
-                    const float4 a = G.spos32[s];
-                    const float dx = X - a.x, dy = Y - a.y, dz = Z - a.z;
-                    const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                    id = __float_as_int(a.w);
-                    if (d2 <= lo) {
-                        acc = true;
-                    } else if (d2 <= hi) {   // ambiguity band: exact FP64 test
-                        const double4_32a q = G.spos[s];
-                        acc = dist2_exact(px, py, pz, q.x, q.y, q.z) <= rs2;
-                    }
-                }
-                const unsigned m = __ballot_sync(0xffffffffu, acc);
-                if (acc) {
-                    const int pos = cnt + __popc(m & ((1u << lane) - 1u));
-                    if (pos < S) list[pos] = id;
-                }
-                cnt += __popc(m);
+    // the test of one candidate slot s of a row ending at s1 (its FP32 record already loaded)
+    auto test = [&](int s, int s1, const float4 &a, int &id) -> bool {
+        if (s >= s1) return false;
+        const float dx = X - a.x, dy = Y - a.y, dz = Z - a.z;
+        const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+        id = __float_as_int(a.w);
+        if (d2 <= lo) return true;
+        if (d2 > hi) return false;
+        const double4_32a q = G.spos[s];   // ambiguity band: exact FP64 test
+        return dist2_exact(px, py, pz, q.x, q.y, q.z) <= rs2;
+    };
+    auto append = [&](bool acc, int id) {
+        const unsigned m = __ballot_sync(0xffffffffu, acc);
+        if (acc) {
+            const int pos = cnt + __popc(m & ((1u << lane) - 1u));
+            if (pos < S) list[pos] = id;
+        }
+        cnt += __popc(m);
+    };
+    // Rows in (z, y) order, r = (kz - z0) ny' + (ky - y0). The candidate ranges of up to 32 rows
+    // are loaded at once, one row per lane, and each row is scanned 64 slots per pass with both
+    // chunks' loads in flight; the accepted IDs keep the order of a plain scan (rows, cells,
+    // slots).
+    const int nyr = y1 - y0 + 1, nrows = nyr * (z1 - z0 + 1);
+    for (int g0 = 0; g0 < nrows; g0 += kWarp) {
+        int r0 = 0, r1 = 0;
+        if (g0 + lane < nrows) {
+            const int r = g0 + lane;
+            const int rowc = ((z0 + r / nyr) * ny + (y0 + r % nyr)) * nx;
+            r0 = G.cell_start[rowc + x0];
+            r1 = G.cell_start[rowc + x1 + 1];
+        }
+        const int ng = min(kWarp, nrows - g0);
+        for (int r = 0; r < ng; r++) {
+            const int s0 = __shfl_sync(0xffffffffu, r0, r), s1 = __shfl_sync(0xffffffffu, r1, r);
+            for (int b = s0; b < s1; b += 2 * kWarp) {
+                const int sa = b + lane, sb = b + kWarp + lane;
+                float4 qa = make_float4(0.f, 0.f, 0.f, 0.f), qb = qa;
+                if (sa < s1) qa = G.spos32[sa];
+                if (sb < s1) qb = G.spos32[sb];
+                int ida = 0, idb = 0;
+                const bool acca = test(sa, s1, qa, ida);
+                const bool accb = test(sb, s1, qb, idb);
+                append(acca, ida);
+                if (b + kWarp < s1) append(accb, idb);
             }
         }
     }
@@ -462,57 +560,6 @@ __device__ __forceinline__ void newton_set_trial(MpNewton &m)
 // One evaluation of the block path (Eq. 14 sums at the pending trial of MP state m): weights
 // into W.w, the sums into m.E (written by one lane per value), m.E[10] = the shift used. If Z
 // over- or underflows, again with the shift at the largest exponent. Warp-uniform.
-// ---- double-float arithmetic for the Hessian sums (FP32 pairs hi + lo, about 2^-47 relative)
-// An FP64 value split into two FP32 values with integer operations on its bits (GB300 charges a
-// conversion instruction an FP64-pipe slot): hi = the leading 24 significant bits, lo = the next
-// 24 of the remaining 29 (truncated), so v = hi + lo to 2^-47 relative. Values outside the normal
-// FP32 range give hi = lo = 0 (the Hessian sums only see weights in [1e-30, 1e30], checked by the
-// caller, and differences of about h).
-__device__ __forceinline__ void df_split(double v, float &hi, float &lo)
-{
-    const int vh = __double2hiint(v);
-    const unsigned vl = (unsigned)__double2loint(v);
-    const int e = ((vh >> 20) & 0x7ff) - 1023;
-    const unsigned sgn = (unsigned)vh & 0x80000000u;
-    const bool ok = e > -126 && e < 128;
-    hi = ok ? __uint_as_float(sgn | ((unsigned)(e + 127) << 23) | ((unsigned)(vh & 0xfffff) << 3) | (vl >> 29))
-            : 0.f;
-    const unsigned r = vl & 0x1fffffffu;   // significand bits 28..0 below hi, weight 2^(e - 52)
-    const int lz = __clz(r);               // >= 3 when r != 0
-    const int el = e - 52 + (31 - lz);     // exponent of r's leading bit
-    lo = (ok && r != 0 && el > -126) ? __uint_as_float(sgn | ((unsigned)(el + 127) << 23) | (((r << lz) << 1) >> 9))
-                                     : 0.f;
-}
-
-// exact widening of an FP32 value to FP64 with integer operations (zero and normal values)
-__device__ __forceinline__ double df_widen(float f)
-{
-    const unsigned b = __float_as_uint(f);
-    const unsigned ef = (b >> 23) & 0xff;
-    if (ef == 0) return 0.0;
-    return __hiloint2double((int)((b & 0x80000000u) | ((ef - 127 + 1023) << 20) | ((b & 0x7fffffu) >> 3)),
-                            (int)(b << 29));
-}
-
-// (p, e) ~ (ah + al)(bh + bl): the product and its error, the al bl term dropped
-__device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float &p, float &e)
-{
-    p = ah * bh;
-    e = fmaf(ah, bh, -p);
-    e = fmaf(ah, bl, e);
-    e = fmaf(al, bh, e);
-}
-
-// (sh, sl) += (q, f) with an error-free sum of the leading parts
-__device__ __forceinline__ void df_add(float &sh, float &sl, float q, float f)
-{
-    const float s = sh + q;
-    const float t = s - sh;
-    const float err = (sh - (s - t)) + (q - t);
-    sl = sl + (err + f);
-    sh = s;
-}
-
 // One evaluation's sums over the pairs of lane `lane`: Z, r = sum w d and A = sum w d d^T.
 // FP64 path (DFH false): all in FP64. Mixed path (DFH true): Z and r in FP64 (r is a cancelling
 // sum that decides convergence at 1e-14 h), the Hessian sums A in double-float: they only set
@@ -543,7 +590,7 @@ __device__ __forceinline__ void lme_acc10(const WarpSmem &W, int n, double s0, d
     for (int k = lane; k < n; k += kWarp) {
         const double x = W.dx[k], y = W.dy[k], z = W.dz[k];
         const double qk = SHIFTED ? W.q[k] + qs : W.q[k];
-        const double wk = exp_scaled(fma(s2, z, fma(s1, y, fma(s0, x, qk))), T);
+        const double wk = exp_scaled<true>(fma(s2, z, fma(s1, y, fma(s0, x, qk))), T);
         W.w[k] = wk;
         v[0] += wk;
         v[1] = fma(wk, x, v[1]); v[2] = fma(wk, y, v[2]); v[3] = fma(wk, z, v[3]);
@@ -714,6 +761,29 @@ size_t lme_smem_bytes(int S, int warps)
 
 size_t search_lme_smem_bytes(int S, int warps) { return lme_smem_bytes(S, warps); }
 
+// The new support of an MP into its row (IDs from the warp's list) and each pair's rank in its
+// node's influence list, by counting with atomics; three slots per lane at a time, so that three
+// atomics (whose old values are waited for) are in flight together. Any order of the ranks gives
+// the same node sums (exact fixed-point sums).
+__device__ __forceinline__ void store_support(const Dev &D, const int32_t *list, int64_t base, int cnt, int lane)
+{
+    for (int k0 = lane; k0 < cnt; k0 += 3 * kWarp) {
+        int id[3], r[3];
+#pragma unroll
+        for (int j = 0; j < 3; j++) id[j] = (k0 + j * kWarp < cnt) ? list[k0 + j * kWarp] : -1;
+#pragma unroll
+        for (int j = 0; j < 3; j++) r[j] = (id[j] >= 0) ? atomicAdd(&D.ncount[id[j]], 1) : 0;
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            if (id[j] < 0) continue;
+            const int64_t k = base + k0 + j * kWarp;
+            D.ids[k] = id[j];
+            if (r[j] > 0xffff) raise_error(D.err, OTM_ERR_CAPACITY, D.ngid[id[j]]);
+            D.rank[k] = (uint16_t)r[j];
+        }
+    }
+}
+
 // ======================================================================== k_search
 __global__ void __launch_bounds__(kSearchWarps * kWarp) k_search(const Dev D)
 {
@@ -738,13 +808,7 @@ __global__ void __launch_bounds__(kSearchWarps * kWarp) k_search(const Dev D)
     // given configuration, so no sort is needed for determinism; exports sort it by ID
     __syncwarp();
     const int64_t base = p * (int64_t)S;
-    for (int k = lane; k < cnt; k += kWarp) {
-        const int id = list[k];
-        D.ids[base + k] = id;
-        const int r = atomicAdd(&D.ncount[id], 1);
-        if (r > 0xffff) raise_error(D.err, OTM_ERR_CAPACITY, D.ngid[id]);
-        D.rank[base + k] = (uint16_t)r;
-    }
+    store_support(D, list, base, cnt, lane);
     if (lane == 0) D.cnt[p] = cnt;
 }
 
@@ -812,6 +876,7 @@ struct KinSum<true> {
         float4 c4 = make_float4(0.f, 0.f, 0.f, 0.f);
         if (n > 0) c4 = D.du32[D.ids[base]];
         c[0] = c4.x; c[1] = c4.y; c[2] = c4.z;
+#pragma unroll 2
         for (int k = lane; k < n; k += kWarp) {
             const int id = D.ids[base + k];
             const double4_32a sh = D.shape[base + k];
@@ -876,13 +941,7 @@ __global__ void __launch_bounds__(kSearchWarps * kWarp) k_kin_search(const Dev D
         return;
     }
     __syncwarp();
-    for (int k = lane; k < cnt; k += kWarp) {
-        const int id = list[k];
-        D.ids[base + k] = id;
-        const int r = atomicAdd(&D.ncount[id], 1);
-        if (r > 0xffff) raise_error(D.err, OTM_ERR_CAPACITY, D.ngid[id]);
-        D.rank[base + k] = (uint16_t)r;
-    }
+    store_support(D, list, base, cnt, lane);
     if (lane == 0) D.cnt[p] = cnt;
 }
 
@@ -1376,13 +1435,14 @@ cudaError_t launch_lme_only(const double *node_x, const double *mp_x, int64_t nm
 // self-test of the table-driven exponential: mine = exp_scaled(y); ref = CUDA's exp of the same
 // argument f = y ln2/1024 carried as a + b (a = fl(y c1), b its rounding error plus y times the
 // low part of ln2/1024), ref = exp(a) (1 + b)
+template <bool DF>
 __global__ void k_exp_selftest(const double *y, int64_t n, double *mine, double *ref)
 {
     __shared__ double T[kExpTable];
     exp_table_load(T);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const double v = y[i];
-        mine[i] = exp_scaled(v, T);
+        mine[i] = exp_scaled<DF>(v, T);
         const double a = v * kExpC1;
         const double b = fma(v, kExpC1, -a) + v * kExpC1lo;
         const double e = exp(a);
@@ -1390,9 +1450,12 @@ __global__ void k_exp_selftest(const double *y, int64_t n, double *mine, double 
     }
 }
 
-cudaError_t launch_exp_selftest(const double *x, int64_t n, double *mine, double *ref, cudaStream_t s)
+cudaError_t launch_exp_selftest(const double *x, int64_t n, bool df, double *mine, double *ref, cudaStream_t s)
 {
-    k_exp_selftest<<<152 * 4, 256, 0, s>>>(x, n, mine, ref);
+    if (df)
+        k_exp_selftest<true><<<152 * 4, 256, 0, s>>>(x, n, mine, ref);
+    else
+        k_exp_selftest<false><<<152 * 4, 256, 0, s>>>(x, n, mine, ref);
     return cudaGetLastError();
 }
 

@@ -126,8 +126,9 @@ def test_fullsize_chip_mixed_with_erosion(orc):
     set is eroded in step 1, and the corner nodes left with no MP within r_s are removed.
     Checked: the surviving MP and node IDs (bit-exact, orphans by brute force over the corner);
     then, through step 2 (support IDs renumbered by the compaction), sampled survivors re-derived
-    by the oracle from the GPU's own state: kinematics (x_p 1e-10; dF to 1e-6 of the MP's strain
-    increment, the FP32 gather of the mixed path), return map, supports (bit-exact), LME."""
+    by the oracle from the GPU's own state: kinematics (to the FP32 gather of the mixed path: x_p
+    within 1e-6 of the support's largest increment, dF within 1e-6 of the MP's strain increment),
+    return map, supports (bit-exact), LME."""
     from paper_2206_08772_gb300.otm import OTM
     p = chip_full(1.5)
     h, Lx, Ly = p.h, p.meta["size"][0], p.meta["size"][1]
@@ -179,9 +180,11 @@ def test_fullsize_chip_mixed_with_erosion(orc):
         assert np.array_equal(ngid2[n2], nid1)
         xp, dF = orc.kinematics(n2.astype(np.int32), shape1[r, :cnt1[r], 0], shape1[r, :cnt1[r], 1:],
                                 st2["node_x"], st2["node_du"])
-        assert np.abs(xp - st2["mp_x"][q2]).max() <= 1e-10 * np.abs(st2["mp_x"]).max()
-        # the mixed path gathers G = sum du (x) e in FP32 (relative to one node's increment): its
-        # dF carries FP32 rounding of the MP's own strain increment
+        # the mixed path gathers the MP displacement and G = sum du (x) e in FP32 (relative to one
+        # node's increment): x_p carries FP32 rounding of the support's increments, dF of the MP's
+        # own strain increment
+        du_sup = np.abs(st2["node_du"][n2]).max()
+        assert np.abs(xp - st2["mp_x"][q2]).max() <= 1e-10 * np.abs(st2["mp_x"]).max() + 1e-6 * du_sup
         assert np.abs(dF - st2["dF"][q2].reshape(3, 3)).max() <= 1e-6 * np.abs(dF - np.eye(3)).max() + 1e-13
         st, sig, be, eb, T, _, failed = orc.return_map(mat, p.dt, st2["dF"][q2].reshape(3, 3), st1["be"][q1],
                                                        st1["ebar"][q1], st1["T"][q1],
