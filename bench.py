@@ -648,7 +648,7 @@ def main():
         mv = world * prob.n_mps * args.steps / (infom["ms"] / 1e3)
         mixed = {"value": mv, "unit": UNIT, "ms_per_step": infom["ms"] / args.steps,
                  "speedup_vs_fp64": mv / value,
-                 "dtype": "f32 scatter/node update, double-float LME Hessian sums, f64 elsewhere",
+                 "dtype": "f32 scatter/node update/kinematics gather, double-float LME Hessian sums and exp polynomial, f64 exponent, Z, residual, F and return map",
                  "phases_ms": phases_m}
     adjoint = None
     if not args.no_adjoint and rank == 0:
