@@ -58,11 +58,12 @@ UNIT = "MP-steps/s"
 #  algorithmic, the method's own work (the exp not counted as flops): per evaluation 25 (exponent
 #  lambda . d + prior: 6; Z, r, J = sum w d d^T: 1 + 6 + 12), once 15 (d_a and the prior term,
 #  N, grad N) and 17 (mass and force contributions): (1 + k) 25 + 32.
-#  executed by this kernel: setup 10 (d, prior exponent), per evaluation 32 (exponent 6, the
-#  table exp's polynomial 7 with its range reduction in integer operations, w d 3, Z 1, r 3,
-#  J 12), final 20 (N 1, e = N d 3, mass 1, force Q e 15): 30 + 32 (1 + k).
+#  executed in FP64 by this kernel: setup 10 (d, prior exponent), per evaluation 29 (exponent 6,
+#  the table exp's two FMAs 4 (its range reduction in integer operations, its polynomial in
+#  double-float on the FP32 pipe), w d 3, Z 1, r 3, J 12), final 20 (N 1, e = N d 3, mass 1,
+#  force Q e 15): 30 + 29 (1 + k).
 LME_ALG_PER_EVAL, LME_ALG_ONCE = 25, 32
-LME_EXEC_PER_EVAL, LME_EXEC_ONCE = 32, 30
+LME_EXEC_PER_EVAL, LME_EXEC_ONCE = 29, 30
 #  k_search (FP32): 8 flops per candidate (3 sub, 1 mul, 2 fma); candidates ~ 3.73 x support.
 #  k_kinematics (FP64): 24 flops per pair (x_p: 3 fma, G = sum du (x) e: 9 fma).
 SEARCH_PER_CAND, CAND_PER_PAIR = 8, 3.73

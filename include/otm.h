@@ -57,9 +57,8 @@ extern "C" {
 #define OTM_PRECISION_FP64 0          /* every step in FP64 */
 #define OTM_PRECISION_MIXED 1         /* FP32 force scatter, node update and kinematics gather (x_p
                                        * increment and G = sum du (x) N d); the LME Newton's Hessian
-                                       * sums and its exponential's polynomial in double-float (FP32
-                                       * pairs, ~2^-47); the exponent, Z, the residual, dF = 1 - G K,
-                                       * F and the return map in FP64 */
+                                       * sums in double-float (FP32 pairs, ~2^-47); the weights, Z,
+                                       * the residual, dF = 1 - G K, F and the return map in FP64 */
 
 #define OTM_FLAG_FIXED 1              /* node flag: displacement increment held at zero */
 
@@ -345,11 +344,9 @@ int otm_lme(const double *node_x, const double *mp_x, int64_t n_mps, const int32
 /* Self-test of the library's internal FP64 exponential (table-driven after Tang, used for the
  * LME weights of Eq. 14). Its argument is scaled: y = f * 1024 / ln 2. Device arrays of n
  * doubles: mine[i] = internal exp of f_i = y[i] ln2/1024; ref[i] = CUDA's exp of the same f_i
- * (carried as a rounded product plus its error, so ref is accurate to about an ulp). precision
- * selects the variant: OTM_PRECISION_FP64 (polynomial in FP64) or OTM_PRECISION_MIXED (the mixed
- * path's, polynomial in double-float); anything else is OTM_ERR_ARG. The first call on a device
- * uploads the exponential's table (synchronous copy). */
-int otm_exp_selftest(const double *y, int64_t n, int32_t precision, double *mine, double *ref, void *stream);
+ * (carried as a rounded product plus its error, so ref is accurate to about an ulp). The first
+ * call on a device uploads the exponential's table (synchronous copy). */
+int otm_exp_selftest(const double *y, int64_t n, double *mine, double *ref, void *stream);
 
 /* Constitutive update (Sec. 4.1 / 4.2) of n_mps points: inputs dF (9), F_new (9, for J),
  * be (6, in/out), ebar, T (in/out); outputs sigma (6), rate, failed (uint8, optional). */

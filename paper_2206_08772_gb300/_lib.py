@@ -89,7 +89,7 @@ _SIGS = {
     "otm_support_search": (C.c_int, [_P, _I64, _P, _I64, _D, _D, _I32, _P, _P, _P, _SZ, _P, _P, _P]),
     "otm_lme": (C.c_int, [_P, _P, _I64, _P, _P, _I32, _D, _D, _I32, _P, _P, _P, _P, _P]),
     "otm_return_map": (C.c_int, [_P, _D, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
-    "otm_exp_selftest": (C.c_int, [_P, _I64, _I32, _P, _P, _P]),
+    "otm_exp_selftest": (C.c_int, [_P, _I64, _P, _P, _P]),
     "otm_snapshot_bytes": (C.c_int, [_P, _P]),
     "otm_snapshot_save": (C.c_int, [_P, _P]),
     "otm_snapshot_load": (C.c_int, [_P, _P]),

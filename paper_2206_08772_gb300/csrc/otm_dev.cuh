@@ -338,7 +338,7 @@ cudaError_t launch_kin_search(const Dev &D, cudaStream_t s, long long *launches)
 cudaError_t launch_lme(const Dev &D, cudaStream_t s, long long *launches);
 cudaError_t launch_node_offsets(const Dev &D, int32_t *tmp, cudaStream_t s, long long *launches);
 cudaError_t exp_table_setup(bool verify = false);
-cudaError_t launch_exp_selftest(const double *x, int64_t n, bool df, double *mine, double *ref, cudaStream_t s);
+cudaError_t launch_exp_selftest(const double *x, int64_t n, double *mine, double *ref, cudaStream_t s);
 cudaError_t launch_node_update(const Dev &D, double t_next, cudaStream_t s, long long *launches);
 cudaError_t launch_rows_to_dense(const void *src, size_t pitch, size_t width, int64_t rows, void *dst, cudaStream_t s);
 cudaError_t launch_rows_from_dense(const void *src, size_t pitch, size_t width, int64_t rows, void *dst,

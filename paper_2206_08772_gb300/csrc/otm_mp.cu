@@ -139,11 +139,11 @@ constexpr float kExpC2h = (float)kExpC2;
 constexpr float kExpC2l = (float)(kExpC2 - (double)kExpC2h);
 constexpr float kExpC3f = (float)kExpC3;
 
-// DF = false: the polynomial p(s) = exp(s ln2/1024) - 1 in FP64 (3 FP64 instructions) and v =
-// T (1 + p) in one FMA. DF = true (mixed path): p in double-float on the FP32 pipe (s split exactly
-// enough: 2^-48 of |s| <= 1/2; p to about 2^-46 of |p| <= 3.4e-4, i.e. 5e-18 absolute), then v =
-// T + T p_hi + T p_lo in two FMAs: two FP64 instructions instead of four, with the same accuracy.
-template <bool DF = false>
+// The polynomial p(s) = exp(s ln2/1024) - 1 (|s| <= 1/2, |p| <= 3.4e-4) runs in double-float on
+// the FP32 pipe: s split into two FP32 values with integer operations (2^-48 of |s|), Horner in
+// error-free FP32 products and sums (p to about 2^-46 of itself: below 5e-18 absolute, against the
+// cubic's own truncation of 5.5e-16), then v = T + T p_hi + T p_lo in two FMAs. The result is as
+// accurate as the same cubic in FP64 Horner form, with two FP64 instructions instead of four.
 __device__ __forceinline__ double exp_scaled(double y, const double *T)
 {
     // y = n + s with n = round(y) and s exact, |s| <= 1/2. For 1 <= |y| < 2^20 (every weight of the
@@ -187,23 +187,17 @@ __device__ __forceinline__ double exp_scaled(double y, const double *T)
     }
     if (n < kExpNmin || n > kExpNmax) return (y > 0.0) ? INFINITY : 0.0;
     const double Tj = T[n & (kExpTable - 1)];
-    double v;
-    if (DF) {
-        float sh, sl;
-        df_split(sr, sh, sl);
-        float ah = kExpC2h, al = kExpC2l;
-        df_add(ah, al, kExpC3f * sh, 0.f);            // C2 + C3 s
-        float bh, bl;
-        df_mul(ah, al, sh, sl, bh, bl);               // (C2 + C3 s) s
-        float ch = kExpC1h, cl = kExpC1l;
-        df_add(ch, cl, bh, bl);                       // C1 + (C2 + C3 s) s
-        float ph, pl;
-        df_mul(ch, cl, sh, sl, ph, pl);               // p
-        v = fma(Tj, df_widen(pl), fma(Tj, df_widen(ph), Tj));
-    } else {
-        const double p = sr * fma(sr, fma(sr, kExpC3, kExpC2), kExpC1);
-        v = fma(Tj, p, Tj);
-    }
+    float sh, sl;
+    df_split(sr, sh, sl);
+    float ah = kExpC2h, al = kExpC2l;
+    df_add(ah, al, kExpC3f * sh, 0.f);            // C2 + C3 s
+    float bh, bl;
+    df_mul(ah, al, sh, sl, bh, bl);               // (C2 + C3 s) s
+    float ch = kExpC1h, cl = kExpC1l;
+    df_add(ch, cl, bh, bl);                       // C1 + (C2 + C3 s) s
+    float ph, pl;
+    df_mul(ch, cl, sh, sl, ph, pl);               // p
+    const double v = fma(Tj, df_widen(pl), fma(Tj, df_widen(ph), Tj));
     return __hiloint2double(__double2hiint(v) + ((n >> 10) << 20), __double2loint(v));
 }
 
@@ -590,7 +584,7 @@ __device__ __forceinline__ void lme_acc10(const WarpSmem &W, int n, double s0, d
     for (int k = lane; k < n; k += kWarp) {
         const double x = W.dx[k], y = W.dy[k], z = W.dz[k];
         const double qk = SHIFTED ? W.q[k] + qs : W.q[k];
-        const double wk = exp_scaled<true>(fma(s2, z, fma(s1, y, fma(s0, x, qk))), T);
+        const double wk = exp_scaled(fma(s2, z, fma(s1, y, fma(s0, x, qk))), T);
         W.w[k] = wk;
         v[0] += wk;
         v[1] = fma(wk, x, v[1]); v[2] = fma(wk, y, v[2]); v[3] = fma(wk, z, v[3]);
@@ -1435,14 +1429,13 @@ cudaError_t launch_lme_only(const double *node_x, const double *mp_x, int64_t nm
 // self-test of the table-driven exponential: mine = exp_scaled(y); ref = CUDA's exp of the same
 // argument f = y ln2/1024 carried as a + b (a = fl(y c1), b its rounding error plus y times the
 // low part of ln2/1024), ref = exp(a) (1 + b)
-template <bool DF>
 __global__ void k_exp_selftest(const double *y, int64_t n, double *mine, double *ref)
 {
     __shared__ double T[kExpTable];
     exp_table_load(T);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const double v = y[i];
-        mine[i] = exp_scaled<DF>(v, T);
+        mine[i] = exp_scaled(v, T);
         const double a = v * kExpC1;
         const double b = fma(v, kExpC1, -a) + v * kExpC1lo;
         const double e = exp(a);
@@ -1450,12 +1443,9 @@ __global__ void k_exp_selftest(const double *y, int64_t n, double *mine, double 
     }
 }
 
-cudaError_t launch_exp_selftest(const double *x, int64_t n, bool df, double *mine, double *ref, cudaStream_t s)
+cudaError_t launch_exp_selftest(const double *x, int64_t n, double *mine, double *ref, cudaStream_t s)
 {
-    if (df)
-        k_exp_selftest<true><<<152 * 4, 256, 0, s>>>(x, n, mine, ref);
-    else
-        k_exp_selftest<false><<<152 * 4, 256, 0, s>>>(x, n, mine, ref);
+    k_exp_selftest<<<152 * 4, 256, 0, s>>>(x, n, mine, ref);
     return cudaGetLastError();
 }
 
