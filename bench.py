@@ -6,14 +6,17 @@ pass of Algorithm 1 over all points (node update, kinematics, return map, linked
 LME shape functions, node-major lists). Metric: material-point-steps/s = n_mps * steps / time.
 
 The configured run is 1000 steps. The cost of a step grows while the elastic wave from the
-impact sweeps the rod (the LME solve needs Newton iterations wherever the material deforms):
-about 140 ms at step 10, 230 ms at step 500, 260 ms from step 550 on. The timed window therefore
-sits mid-run: --start-step untimed steps (default 500), then W warm-up and K timed steps.
+impact sweeps the rod (the LME solve needs Newton iterations wherever the material deforms), so
+the timed window sits mid-run: --start-step untimed steps (default 500), then W warm-up and K
+timed steps.
 
-value       : FP64 path, inputs resident in HBM, CUDA events on the library's stream.
+value       : FP64 path (--precision mixed: the mixed path alone), inputs resident in HBM, CUDA
+              events on the library's stream.
 whole_run   : the same metric over all 1000 configured steps of the run (the spin-up, the window
               and the rest, each timed with CUDA events).
-mixed       : the FP32-scatter / FP64-Newton path, from the FP64 path's state at the same step.
+mixed       : the mixed path (FP32 force scatter, node update and kinematics gather; double-float
+              Newton Hessian sums; FP64 weights, residual, F and return map), from the FP64 path's
+              state at the same step.
 adjoint     : adjoint/forward time ratio of the hand-written GPU adjoint on the 202,752-MP rod.
 e2e         : the same metric through the C ABI from page-locked host memory: the state at the
               window's start loaded from a host snapshot (H2D of every node, MP and support array),
@@ -52,6 +55,8 @@ import scenarios  # noqa: E402
 
 METRIC = "material-point-steps/s on 1 GB300 (FP64 vs mixed); adjoint/forward time ratio"
 UNIT = "MP-steps/s"
+MIXED_DTYPE = ("f32 scatter/node update/kinematics gather, double-float LME Hessian sums, "
+               "f64 exponent, Z, residual, F and return map")
 
 # Arithmetic per pair of the LME kernel (FP64; an FMA counts 2 flops), Newton evaluations per
 # solve = 1 + k (k the mean Newton iterations, measured):
@@ -557,6 +562,8 @@ def main():
     ap.add_argument("--workload", default="taylor_jc_h0.12")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+                    help="path of the main timed run (mixed: the mixed path alone, no second leg)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-whole-run", action="store_true")
@@ -621,7 +628,7 @@ def main():
         return
 
     with ClockSampler(local) as clk:
-        sim, info = time_gpu(prob, "fp64", args.steps, args.warmup, torch, dist, start=args.start_step,
+        sim, info = time_gpu(prob, args.precision, args.steps, args.warmup, torch, dist, start=args.start_step,
                              save_snaps=True, profile_window=args.profile_window,
                              save_state=not args.no_cpu_baseline and rank == 0)
     snap_dev, snap_host = info.pop("snaps")
@@ -640,7 +647,7 @@ def main():
                          "phase-profiled steps by wall clock" % args.run_steps}
 
     mixed = None
-    if not args.no_mixed:
+    if not args.no_mixed and args.precision == "fp64":
         simm, infom = time_gpu(prob, "mixed", args.steps, args.warmup, torch, dist, snap=snap_dev)
         phases_m, _ = phase_profile(simm)
         simm.close()
@@ -649,7 +656,7 @@ def main():
         mv = world * prob.n_mps * args.steps / (infom["ms"] / 1e3)
         mixed = {"value": mv, "unit": UNIT, "ms_per_step": infom["ms"] / args.steps,
                  "speedup_vs_fp64": mv / value,
-                 "dtype": "f32 scatter/node update/kinematics gather, double-float LME Hessian sums and exp polynomial, f64 exponent, Z, residual, F and return map",
+                 "dtype": MIXED_DTYPE,
                  "phases_ms": phases_m}
     adjoint = None
     if not args.no_adjoint and rank == 0:
@@ -689,10 +696,13 @@ def main():
     kd = kernels[dom]
     roofline = {"kernel": f"k_{dom}", "bound": "alu", "achieved": kd["achieved_tflops"], "peak": kd["peak"],
                 "unit": "TFLOP/s", "frac": kd["frac"],
-                "frac_executed": (lme_exec / (kd["ms"] / 1e3) / kd["peak"]) if dom == "lme" else None,
+                # the executed-flop count and the captured DRAM bytes are those of the FP64 path's kernel
+                "frac_executed": ((lme_exec / (kd["ms"] / 1e3) / kd["peak"])
+                                  if dom == "lme" and args.precision == "fp64" else None),
                 "flops_per_pair": {"algorithmic": LME_ALG_PER_EVAL * (1 + k_bar) + LME_ALG_ONCE,
-                                   "executed": LME_EXEC_PER_EVAL * (1 + k_bar) + LME_EXEC_ONCE},
-                "traffic": LME_DRAM_BYTES_PER_PAIR * pairs if dom == "lme" else None,
+                                   "executed": (LME_EXEC_PER_EVAL * (1 + k_bar) + LME_EXEC_ONCE
+                                                if args.precision == "fp64" else None)},
+                "traffic": LME_DRAM_BYTES_PER_PAIR * pairs if dom == "lme" and args.precision == "fp64" else None,
                 "traffic_note": ("bytes per launch: DRAM bytes per pair of the ncu capture on the 202,752-MP rod "
                                  "(profiles/) x this launch's pairs"),
                 "peak_source": ("derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz (no FP64 entry in the "
@@ -707,7 +717,8 @@ def main():
         cpu_all = {k: o[k] for k in ("value", "unit", "cores", "kind", "sample")}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
+            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else MIXED_DTYPE, "data": "synthetic",
+            "config": config,
             "gpu_launches": info["launches"], "whole_run": whole, "mixed": mixed, "e2e": e2e,
             "roofline": roofline, "adjoint": adjoint, "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all,
             "chip": chip, "clocks": clk.summary(),
