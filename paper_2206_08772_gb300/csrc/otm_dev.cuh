@@ -87,6 +87,8 @@ struct Dev {
     uint8_t *failed;                 // fracture flags of the step
     uint8_t *lme_fail;               // LME failures of the step (node insertion)
     int32_t *n_fail;                 // their count
+    int32_t *lme_defer;              // MPs whose support exceeds k_lme's shared-memory rows
+    int32_t *n_defer;                // their count (k_lme_wide solves them)
     int32_t *flag;                   // one int of scratch for host-read checks (argument validation)
     int64_t *mgid;
     // pairs: MP-major padded rows (ids, shape, rank) and node-major contributions

@@ -984,20 +984,27 @@ __device__ __forceinline__ void lme_record(const Dev &D, int64_t p, double l0, d
     D.lam[3 * p + 2] = l2;
 }
 
+// Shared-memory rows per MP in k_lme. With 336 slots a block of 4 MPs takes 55 KB and 4 blocks
+// fit an SM (3 with full 384-slot rows), which hides more of the FP64 pipe's dependency and
+// barrier stalls; the supports of the benchmark rods stay below (at most 316 slots mid-run on the
+// 2.85 M-MP rod). MPs with larger supports are deferred to k_lme_wide, which runs the same block
+// code with rows of the full capacity S, so either launch gives the same bits.
+constexpr int kLmeRows = 336;
+
+__host__ __device__ __forceinline__ int lme_rows(int S) { return S < kLmeRows ? S : kLmeRows; }
+
+// The LME solve of the block's MPs (one per warp; p the warp's MP, active whether it has one),
+// shared-memory rows of `rows` slots. Every thread of the block calls it (block barriers inside);
+// the exponential's table is read from global memory (L1-resident, 8 KB).
 template <bool MIXED, bool STAB>
-__global__ void __launch_bounds__(kLmeWarps * kWarp) k_lme(const Dev D)
+__device__ __forceinline__ void lme_block(const Dev &D, int64_t p, bool active, int rows, unsigned char *smem_raw)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    double *T = (double *)smem_raw;
-    exp_table_load(T);
+    const double *__restrict__ T = g_exp2_table;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t p = (int64_t)blockIdx.x * kLmeWarps + warp;
     const int S = D.S;
-    MpNewton *NS =
-        (MpNewton *)(smem_raw + kExpTable * sizeof(double) + (size_t)kLmeWarps * 5 * (size_t)S * sizeof(double));
+    MpNewton *NS = (MpNewton *)(smem_raw + (size_t)kLmeWarps * 5 * (size_t)rows * sizeof(double));
     // every warp reaches the block barriers below; idle warps skip the work
-    const bool active = (p < D.nm) && !has_error(D.err);
-    WarpSmem W = warp_smem(smem_raw + kExpTable * sizeof(double), S, warp);
+    WarpSmem W = warp_smem(smem_raw, rows, warp);
     const int64_t base = p * (int64_t)S;
     MpNewton &M = NS[warp];
     int cnt = 0;
@@ -1173,23 +1180,64 @@ __global__ void __launch_bounds__(kLmeWarps * kWarp) k_lme(const Dev D)
 }
 
 template <bool MIXED, bool STAB>
-static cudaError_t launch_lme_t(const Dev &D, cudaStream_t s, size_t smem, unsigned blocks)
+__global__ void __launch_bounds__(kLmeWarps * kWarp) k_lme(const Dev D)
 {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int64_t p = (int64_t)blockIdx.x * kLmeWarps + (threadIdx.x >> 5);
+    const int rows = lme_rows(D.S);
+    bool active = (p < D.nm) && !has_error(D.err);
+    if (active && D.cnt[p] > rows) {   // solved by k_lme_wide
+        if (lane == 0) D.lme_defer[atomicAdd(D.n_defer, 1)] = (int32_t)p;
+        active = false;
+    }
+    lme_block<MIXED, STAB>(D, p, active, rows, smem_raw);
+}
+
+// the deferred MPs, 4 per block and round, with rows of the full capacity S (grid-stride over the
+// list, whose length the previous launch left in *n_defer)
+template <bool MIXED, bool STAB>
+__global__ void __launch_bounds__(kLmeWarps * kWarp) k_lme_wide(const Dev D)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n = *D.n_defer;
+    for (int g = blockIdx.x; g * kLmeWarps < n; g += gridDim.x) {
+        const int i = g * kLmeWarps + (threadIdx.x >> 5);
+        const int64_t p = (i < n) ? (int64_t)D.lme_defer[i] : -1;
+        lme_block<MIXED, STAB>(D, p, p >= 0 && !has_error(D.err), D.S, smem_raw);
+    }
+}
+
+static size_t lme_block_smem(int rows)
+{
+    return (size_t)kLmeWarps * 5 * (size_t)rows * sizeof(double) + (size_t)kLmeWarps * sizeof(MpNewton);
+}
+
+template <bool MIXED, bool STAB>
+static cudaError_t launch_lme_t(const Dev &D, cudaStream_t s, unsigned blocks)
+{
+    const size_t smem = lme_block_smem(lme_rows(D.S)), smem_wide = lme_block_smem(D.S);
     cudaError_t e = cudaFuncSetAttribute(k_lme<MIXED, STAB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_lme_wide<MIXED, STAB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_wide);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(D.n_defer, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return e;
     k_lme<MIXED, STAB><<<blocks, kLmeWarps * kWarp, smem, s>>>(D);
+    // one persistent round of blocks over the deferred MPs (none on most steps: the launch then
+    // returns at once)
+    k_lme_wide<MIXED, STAB><<<152 * 3, kLmeWarps * kWarp, smem_wide, s>>>(D);
     return cudaGetLastError();
 }
 
 cudaError_t launch_lme(const Dev &D, cudaStream_t s, long long *launches)
 {
-    const size_t smem = lme_smem_bytes(D.S, kLmeWarps);
     const unsigned blocks = (unsigned)((D.nm + kLmeWarps - 1) / kLmeWarps);
     if (blocks == 0) return cudaSuccess;
     const bool mixed = D.precision == OTM_PRECISION_MIXED, stab = D.eps_stab > 0.0;
-    cudaError_t e = mixed ? (stab ? launch_lme_t<true, true>(D, s, smem, blocks) : launch_lme_t<true, false>(D, s, smem, blocks))
-                          : (stab ? launch_lme_t<false, true>(D, s, smem, blocks) : launch_lme_t<false, false>(D, s, smem, blocks));
-    if (launches) *launches += 1;
+    cudaError_t e = mixed ? (stab ? launch_lme_t<true, true>(D, s, blocks) : launch_lme_t<true, false>(D, s, blocks))
+                          : (stab ? launch_lme_t<false, true>(D, s, blocks) : launch_lme_t<false, false>(D, s, blocks));
+    if (launches) *launches += 2;
     return e;
 }
 

@@ -77,6 +77,30 @@ def test_fp64_config1_full_100_steps(orc, OTM):
     assert abs(m.sum() - p.mp_mass.sum()) <= 1e-12 * p.mp_mass.sum()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_supports_beyond_the_lme_shared_rows(orc, OTM, precision):
+    """The LME kernel keeps 336 of the 384 support slots per MP in shared memory; MPs with larger
+    supports are solved by a second launch with full rows. With a support tolerance of 3e-7
+    (r_s = 4.33 h) a rod of R 4.8 mm has 672 of its 8,064 MPs above 336 nodes at the start: after
+    12 steps the FP64 path matches the oracle (supports bit-exact, every field 1e-10), the mixed
+    path within its own bounds, and supports above 336 are still present."""
+    p = scenarios.taylor_rod(h=0.8e-3, R=4.8e-3, L=9.6e-3, material=scenarios.copper_jc(), support_tol=3e-7)
+    sim_o = orc.Sim(p)
+    sim_g = OTM(p, precision=precision)
+    assert np.diff(sim_o.get("offsets")).max() > 336
+    assert sim_g.step(12) == 0, sim_g.error()
+    assert sim_o.step(12) == 0
+    cnt = np.diff(sim_g.supports()[0])
+    assert 336 < cnt.max() <= 384
+    if precision == "fp64":
+        assert supports_equal(sim_g, sim_o)
+        errs, bad = compare(sim_g, sim_o, {"default": 1e-10})
+    else:
+        errs, bad = compare(sim_g, sim_o, {"default": 1e-4, "node_x": 1e-7, "mp_x": 1e-7})
+    print("wide supports", precision, int((cnt > 336).sum()), errs)
+    assert not bad, bad
+
+
 def test_mixed_path_error_table(orc, OTM):
     p = scenarios.taylor_rod(h=0.8e-3, R=3.2e-3, L=9.6e-3, material=scenarios.copper_jc())
     sim_o = orc.Sim(p)
