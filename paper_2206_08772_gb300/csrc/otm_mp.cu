@@ -898,8 +898,11 @@ struct KinSum<true> {
 // per MP: the gather over the old support gives x_p and dF, then the candidate scan builds the
 // new support in the same row. Used when no erosion can remove MPs between the two; the
 // return map (which only needs dF) follows.
+// Occupancy: the mixed kernel is bound by memory latency (the FP32 gather leaves the FP64 pipe
+// idle), so 12 blocks per SM (40 registers, a 16-byte spill) beat 10 (48 registers): 14.2 against
+// 14.8 ms on the 2.85 M-MP rod; the FP64 kernel is bound by its FP64 gather and takes 8 blocks.
 template <bool MIXED>
-__global__ void __launch_bounds__(kSearchWarps * kWarp) k_kin_search(const Dev D)
+__global__ void __launch_bounds__(kSearchWarps * kWarp, MIXED ? 12 : 8) k_kin_search(const Dev D)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
