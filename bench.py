@@ -74,9 +74,9 @@ LME_EXEC_PER_EVAL, LME_EXEC_ONCE = 29, 30
 SEARCH_PER_CAND, CAND_PER_PAIR = 8, 3.73
 KIN_PER_PAIR = 24
 # DRAM bytes per pair of one k_lme launch, from the ncu capture of the h 0.29 mm rod at step 302
-# (dram__bytes_read.sum + dram__bytes_write.sum = 3.825 GB over 54.11 M pairs); the traffic of
+# (dram__bytes_read.sum + dram__bytes_write.sum = 3.959 GB over 54.11 M pairs); the traffic of
 # a launch scales with its pairs (shape and contribution writes, ID and rank reads)
-LME_DRAM_BYTES_PER_PAIR = (0.394587e9 + 3.430532e9) / (202752 * 266.871)
+LME_DRAM_BYTES_PER_PAIR = (0.395994e9 + 3.563405e9) / (202752 * 266.871)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 2 FP64 FMA lanes / SM / clock at 2070 MHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
