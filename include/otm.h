@@ -113,14 +113,17 @@ typedef struct otm_handle otm_handle;
  *  MP_X: 24 n_mps  F, DF: 72 n_mps  BE, SIGMA: 48 n_mps  VOL, EBAR, T, RATE: 8 n_mps
  *  LAMBDA: 24 n_mps  SUPPORT_COUNT, NEWTON_IT: 4 n_mps
  *  SUPPORT_IDS: 4 n_mps max_support (padded rows, row p holds SUPPORT_COUNT[p] IDs, ascending)
- *  SHAPE: 32 n_mps max_support (padded rows of (N, dN/dx, dN/dy, dN/dz))
- *  MP_GID, NODE_GID: 8 * count (original IDs of the surviving entries) */
+ *  SHAPE: 32 n_mps max_support (padded rows of (N, dN/dx, dN/dy, dN/dz); in the mixed path the
+ *         gradients carry FP32 rounding: e = N d is formed in FP32 there)
+ *  MP_GID, NODE_GID: 8 * count (original IDs of the surviving entries)
+ *  KINV: 48 n_mps (J^-1 of each MP's last LME solve, xx yy zz xy yz xz: grad N_a = -J^-1 N_a d_a) */
 enum {
     OTM_FIELD_NODE_X = 0, OTM_FIELD_NODE_DU = 1, OTM_FIELD_NODE_MASS = 2, OTM_FIELD_NODE_FORCE = 3,
     OTM_FIELD_MP_X = 4, OTM_FIELD_F = 5, OTM_FIELD_BE = 6, OTM_FIELD_SIGMA = 7, OTM_FIELD_VOL = 8,
     OTM_FIELD_EBAR = 9, OTM_FIELD_T = 10, OTM_FIELD_LAMBDA = 11, OTM_FIELD_SUPPORT_COUNT = 12,
     OTM_FIELD_SUPPORT_IDS = 13, OTM_FIELD_SHAPE = 14, OTM_FIELD_NEWTON_IT = 15, OTM_FIELD_RATE = 16,
-    OTM_FIELD_DF = 17, OTM_FIELD_MP_GID = 18, OTM_FIELD_NODE_GID = 19, OTM_FIELD_NODE_FLAGS = 20
+    OTM_FIELD_DF = 17, OTM_FIELD_MP_GID = 18, OTM_FIELD_NODE_GID = 19, OTM_FIELD_NODE_FLAGS = 20,
+    OTM_FIELD_KINV = 21
 };
 
 /* Bytes of device workspace needed for a problem of this size. */
@@ -273,7 +276,8 @@ int otm_snapshot_load(otm_handle *h, const void *src);
 /* Bytes of the adjoint workspace (device memory, 256-byte aligned, caller-owned). */
 int otm_adjoint_bytes(otm_handle *h, size_t *bytes);
 /* Start a backward pass at the current (final) state: xbar_host (n_nodes x 3, host) is
- * d objective / d node positions; every other adjoint starts at zero. */
+ * d objective / d node positions; every other adjoint starts at zero. The handle must be an
+ * FP64-path handle without erosion, insertion or stabilisation (otherwise OTM_ERR_ARG). */
 int otm_adjoint_begin(otm_handle *h, void *adj_ws, size_t bytes, const double *xbar_host);
 /* One backward step. Precondition: the handle holds state n (e.g. from otm_snapshot_load) and
  * the adjoint workspace holds the adjoint of state n+1. The call needs state n+1 and the node

@@ -26,7 +26,7 @@ PHASES = ["node_update", "kinematics", "return_map", "grid", "search", "node_maj
 
 FIELD = dict(node_x=0, node_du=1, node_mass=2, node_force=3, mp_x=4, F=5, be=6, sigma=7, vol=8,
              ebar=9, T=10, lam=11, support_count=12, support_ids=13, shape=14, newton_it=15,
-             rate=16, dF=17, mp_gid=18, node_gid=19, node_flags=20)
+             rate=16, dF=17, mp_gid=18, node_gid=19, node_flags=20, kinv=21)
 
 
 class OTMError(RuntimeError):

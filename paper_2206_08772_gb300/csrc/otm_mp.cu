@@ -1128,7 +1128,19 @@ __device__ __forceinline__ void lme_block(const Dev &D, int64_t p, bool active, 
         const double wk = W.w[k];
         const double N = wk * iZ;
         const double x = W.dx[k], y = W.dy[k], z = W.dz[k];
-        const double ex = N * x, ey = N * y, ez = N * z;
+        double ex, ey, ez;
+        float fN = 0.f, fex = 0.f, fey = 0.f, fez = 0.f;
+        if (MIXED) {
+            // e = N d in FP32 (every consumer of the mixed path's rows rounds them to FP32),
+            // stored widened exactly; N stays FP64
+            fN = f32_round_bits(N);
+            fex = fN * f32_round_bits(x);
+            fey = fN * f32_round_bits(y);
+            fez = fN * f32_round_bits(z);
+            ex = df_widen(fex); ey = df_widen(fey); ez = df_widen(fez);
+        } else {
+            ex = N * x; ey = N * y; ez = N * z;
+        }
         D.shape[base + k] = make_double4_32a(N, ex, ey, ez);
         const int id = D.ids[base + k];
         const int64_t pos = (int64_t)D.noff[id] + D.rank[base + k];
@@ -1145,9 +1157,7 @@ __device__ __forceinline__ void lme_block(const Dev &D, int64_t p, bool active, 
             }
         }
         if (MIXED) {
-            // FP32 operands by integer rounding of the FP64 row (no FP64-pipe conversions)
-            const float fex = f32_round_bits(ex), fey = f32_round_bits(ey), fez = f32_round_bits(ez);
-            const float c0 = mpf * f32_round_bits(N);
+            const float c0 = mpf * fN;
             float c1 = fmaf(Qf[2], fez, fmaf(Qf[1], fey, Qf[0] * fex));
             float c2 = fmaf(Qf[5], fez, fmaf(Qf[4], fey, Qf[3] * fex));
             float c3 = fmaf(Qf[8], fez, fmaf(Qf[7], fey, Qf[6] * fex));

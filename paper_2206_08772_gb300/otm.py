@@ -19,7 +19,7 @@ _WIDTH = dict(node_x=(3, np.float64), node_du=(3, np.float64), node_mass=(1, np.
               F=(9, np.float64), dF=(9, np.float64), be=(6, np.float64), sigma=(6, np.float64),
               vol=(1, np.float64), ebar=(1, np.float64), T=(1, np.float64), rate=(1, np.float64),
               lam=(3, np.float64), support_count=(1, np.int32), newton_it=(1, np.int32),
-              mp_gid=(1, np.int64), node_gid=(1, np.int64))
+              mp_gid=(1, np.int64), node_gid=(1, np.int64), kinv=(6, np.float64))
 
 
 def material_struct(m) -> Material:

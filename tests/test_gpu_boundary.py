@@ -129,6 +129,22 @@ def test_keep_last_good_undoes_the_failing_step(OTM, host):
         assert rel(g.get(f), ref.get(f)) <= 1e-10, f
 
 
+def test_adjoint_refuses_a_mixed_path_handle(OTM):
+    """The adjoint differentiates the FP64 step: otm_adjoint_begin on a mixed-path handle is
+    OTM_ERR_ARG, and the same problem in FP64 starts."""
+    from paper_2206_08772_gb300._lib import ERR_ARG, OTMError
+    p = scenarios.taylor_rod(h=0.8e-3, R=3.2e-3, L=6.4e-3, material=scenarios.copper_jc())
+    m = OTM(p, precision="mixed")
+    assert m.step(2) == 0
+    xbar = np.zeros((p.n_nodes, 3))
+    with pytest.raises(OTMError) as ei:
+        m.adjoint_begin(xbar)
+    assert ei.value.code == ERR_ARG
+    a = OTM(p, precision="fp64")
+    assert a.step(2) == 0
+    a.adjoint_begin(xbar)
+
+
 def test_far_node_makes_the_grid_too_large_not_a_fault(OTM):
     """200,000 nodes in a small box plus one node 3000 m away on every axis: each axis has
     about 3e6 cells of 1 mm, within the per-axis limit (16 n + 65536 cells), but their product

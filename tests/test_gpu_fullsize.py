@@ -128,7 +128,7 @@ def test_fullsize_chip_mixed_with_erosion(orc):
     then, through step 2 (support IDs renumbered by the compaction), sampled survivors re-derived
     by the oracle from the GPU's own state: kinematics (to the FP32 gather of the mixed path: x_p
     within 1e-6 of the support's largest increment, dF within 1e-6 of the MP's strain increment),
-    return map, supports (bit-exact), LME."""
+    return map, supports (bit-exact), LME (N 1e-10; grad N 1e-6, its e = N d being FP32)."""
     from paper_2206_08772_gb300.otm import OTM
     p = chip_full(1.5)
     h, Lx, Ly = p.h, p.meta["size"][0], p.meta["size"][1]
@@ -200,7 +200,8 @@ def test_fullsize_chip_mixed_with_erosion(orc):
         s_, N, dN, _, _ = orc.lme(st2["mp_x"][q2] - st2["node_x"][sup], p.beta, p.newton_tol * p.h)
         assert s_ == 0
         shp = sim.get_rows("shape", [q2])[0]
-        assert rel(shp[:n, 0], N) <= 1e-10 and rel(shp[:n, 1:], dN) <= 1e-10
+        # N in FP64; the mixed path forms e = N d, hence grad N = -J^-1 e, in FP32
+        assert rel(shp[:n, 0], N) <= 1e-10 and rel(shp[:n, 1:], dN) <= 1e-6
         checked += 1
     assert checked >= 24 and plastic > 0
 
