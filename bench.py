@@ -55,8 +55,8 @@ import scenarios  # noqa: E402
 
 METRIC = "material-point-steps/s on 1 GB300 (FP64 vs mixed); adjoint/forward time ratio"
 UNIT = "MP-steps/s"
-MIXED_DTYPE = ("f32 scatter/node update/kinematics gather, double-float LME Hessian sums, "
-               "f64 exponent, Z, residual, F and return map")
+MIXED_DTYPE = ("f32 scatter/node update/kinematics gather/row N d, double-float LME Hessian sums, "
+               "f64 exponent, N, Z, residual, F and return map")
 
 # Arithmetic per pair of the LME kernel (FP64; an FMA counts 2 flops), Newton evaluations per
 # solve = 1 + k (k the mean Newton iterations, measured):

@@ -55,10 +55,11 @@ extern "C" {
 #define OTM_ERR_CAPACITY (-8)         /* support / influence / cell capacity exceeded */
 
 #define OTM_PRECISION_FP64 0          /* every step in FP64 */
-#define OTM_PRECISION_MIXED 1         /* FP32 force scatter, node update and kinematics gather (x_p
-                                       * increment and G = sum du (x) N d); the LME Newton's Hessian
-                                       * sums in double-float (FP32 pairs, ~2^-47); the weights, Z,
-                                       * the residual, dF = 1 - G K, F and the return map in FP64 */
+#define OTM_PRECISION_MIXED 1         /* FP32 force scatter, node update, pair rows' e = N d and
+                                       * kinematics gather (x_p increment and G = sum du (x) N d);
+                                       * the LME Newton's Hessian sums in double-float (FP32 pairs,
+                                       * ~2^-47); the weights, N, Z, the residual, dF = 1 - G K, F
+                                       * and the return map in FP64 */
 
 #define OTM_FLAG_FIXED 1              /* node flag: displacement increment held at zero */
 
