@@ -747,13 +747,13 @@ __device__ void newton_round(MpNewton &m, double tol, int max_it)
     newton_set_trial(m);
 }
 
+// shared memory of the stand-alone LME kernel (k_lme_only): the exp table and rows of S slots
 size_t lme_smem_bytes(int S, int warps)
 {
     return kExpTable * sizeof(double) + (size_t)warps * 5 * (size_t)S * sizeof(double) +
            (size_t)warps * sizeof(MpNewton);
 }
 
-size_t search_lme_smem_bytes(int S, int warps) { return lme_smem_bytes(S, warps); }
 
 // The new support of an MP into its row (IDs from the warp's list) and each pair's rank in its
 // node's influence list, by counting with atomics; three slots per lane at a time, so that three
