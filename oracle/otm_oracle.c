@@ -457,6 +457,16 @@ static int return_map(const orc_material *M, double dt, const double dF[3][3], c
                 x = xn;
             }
             if (!ok) return ORC_ERR_RETURNMAP_NOCONV;
+            /* one more Newton step from the accepted iterate: |g| <= 1e-12 q_tr fixes x only to
+             * that tolerance, and the step (quadratic convergence) fixes it to rounding, so the
+             * increment does not depend on where the iteration started */
+            {
+                double sy, dsy;
+                jc_flow(M, ebar_n, x, dt, T_n, &sy, &dsy);
+                double g = q_tr - 3.0 * mu * x - sy;
+                double xn = x - g / (-3.0 * mu - dsy);
+                if (xn > lo && xn < hi) x = xn;
+            }
             dep = x;
         }
     }

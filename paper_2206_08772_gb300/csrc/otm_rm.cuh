@@ -161,6 +161,14 @@ __device__ inline int return_map_point(const otm_material &M, double dt, const R
                 x = xn;
             }
             if (!ok) return OTM_ERR_RETURNMAP_NOCONV;
+            {   // one more Newton step: the accepted iterate is fixed only to the tolerance, the
+                // step fixes it to rounding, whatever the start (warm or the bracket's midpoint)
+                double sy, dsy;
+                jc_sigma_y(M, in.ebar, x, dt, therm, sy, dsy);
+                const double g = q_tr - 3.0 * mu * x - sy;
+                const double xn = x - g / (-3.0 * mu - dsy);
+                if (xn > lo && xn < hi) x = xn;
+            }
             dep = x;
         }
     }

@@ -113,6 +113,36 @@ def test_mixed_path_error_table(orc, OTM):
     assert not bad, bad
 
 
+def test_per_field_error_through_the_impact(orc, OTM):
+    """The error of each output field against the FP64 oracle (its OpenMP build, the same
+    arithmetic as the serial one), max |gpu - oracle| / max |oracle| over the field, for both GPU
+    paths on the Johnson-Cook rod at h 0.6 mm (R 3.2, L 25.4 mm, 22,176 MPs) at steps 50, 100 and
+    200 of the impact: the FP64 path within 1e-10; the mixed path within 1e-4 (positions 1e-7),
+    its error set by the FP32 force contributions and kinematics gather."""
+    p = scenarios.taylor_rod(h=0.6e-3, material=scenarios.copper_jc())
+    sim_o = orc.Sim(p, omp=True)
+    g64 = OTM(p, precision="fp64")
+    g32 = OTM(p, precision="mixed")
+    table = {"fp64": {}, "mixed": {}}
+    bad_all = []
+    done = 0
+    for n in (50, 100, 200):
+        assert sim_o.step(n - done) == 0
+        assert g64.step(n - done) == 0, g64.error()
+        assert g32.step(n - done) == 0, g32.error()
+        done = n
+        for name, sim in (("fp64", g64), ("mixed", g32)):
+            tol = {"default": 1e-10} if name == "fp64" else {"default": 1e-4, "node_x": 1e-7, "mp_x": 1e-7}
+            errs, bad = compare(sim, sim_o, tol)
+            table[name][n] = errs
+            if bad:
+                bad_all.append((name, n, bad))
+    for name in ("fp64", "mixed"):
+        for n, errs in table[name].items():
+            print("per-field error", name, "step", n, " ".join(f"{f} {e:.1e}" for f, e in errs.items()))
+    assert not bad_all, bad_all
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_determinism(OTM, precision):
     p = scenarios.taylor_rod(h=0.8e-3, R=3.2e-3, L=6.4e-3, material=scenarios.copper_jc())
