@@ -20,7 +20,7 @@
 namespace otm {
 
 // ======================================================================== double-float arithmetic
-// FP32 pairs hi + lo, about 2^-47 relative (the mixed path's Hessian sums and exp polynomial)
+// FP32 pairs hi + lo, about 2^-47 relative (the exp's polynomial, the mixed path's Hessian sums)
 // An FP64 value split into two FP32 values with integer operations on its bits (GB300 charges a
 // conversion instruction an FP64-pipe slot): hi = the leading 24 significant bits, lo = the next
 // 24 of the remaining 29 (truncated), so v = hi + lo to 2^-47 relative. Values outside the normal
@@ -80,7 +80,8 @@ __device__ __forceinline__ void df_add(float &sh, float &sl, float q, float f)
 //   exp(f) = 2^(n >> 10) * 2^((n & 1023) / 1024) * exp(s ln2 / 1024),
 // with exp(t) - 1 for |t| <= ln2/2048 by its Taylor polynomial of degree 3 (truncation below
 // 5.5e-16 relative). The 1024-entry table 2^(j/1024) is computed once on the host (C library
-// exp2) into g_exp2_table and staged into each block's shared memory. Valid for f in about
+// exp2) into g_exp2_table; the LME step kernel reads it through L1, the stand-alone kernels stage
+// it into shared memory. Valid for f in about
 // [-707, 708]; below it returns 0 (a weight below 1e-307 of the largest), above +inf (the caller
 // then re-shifts). The scaling rounds y like any FP64 argument, so the result carries
 // |f| * 2^-53 relative error from it, plus about 3 ulps.
